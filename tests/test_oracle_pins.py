@@ -1,0 +1,548 @@
+"""Pins of the FP64 oracle to facts outside itself (CPU only).
+
+Each test checks the oracle against something the mathematics or the paper
+fixes: conservation laws, the closed-form decay of discrete Fourier modes, the
+linear-quadratic survival law inside a binomial confidence interval, the
+deterministic age-structured conveyor of the cell cycle, combinatorial
+properties of the division rule, the paper's protocol semantics, and brute
+force on tiny lattices.  A plausible slip anywhere in oracle.c (a dropped term,
+a wrong sign or index, a swapped field) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats as sps
+
+from synth.params import (P0, F_DEFAULT, F_DIVISION, F_DEATH, F_QUIESCENCE, F_REACTION, F_DIFFUSION,
+                          EMPTY, G1, S, G2, M, Q)
+
+SEED = 0x1234_5678_9ABC
+
+
+def _coords(L):
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    return x.ravel(), y.ravel(), z.ravel()
+
+
+# ----------------------------------------------------------------------------- Philox
+def test_philox_uniform_and_independent(orc):
+    n = 1 << 14
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n)
+    ctr[:, 1] = 7
+    outs = {}
+    for purpose in (0, 1, 2):
+        ctr[:, 2] = purpose
+        outs[purpose] = orc.philox(ctr, SEED)
+    u = {k: (v[:, 0] >> 8).astype(np.float64) / 2 ** 24 for k, v in outs.items()}
+    for k in u:
+        assert sps.kstest(u[k], "uniform").pvalue > 1e-3
+        hist = np.bincount((u[k] * 64).astype(int), minlength=64)
+        assert sps.chisquare(hist).pvalue > 1e-3
+    # distinct purposes give uncorrelated streams
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        r = np.corrcoef(u[a], u[b])[0, 1]
+        assert abs(r) < 4.0 / math.sqrt(n)
+    # a bijection of the counter for a fixed key: no collisions among 2^14 outputs
+    packed = {tuple(r) for r in outs[0]}
+    assert len(packed) == n
+    # all four output words are uniform bytes
+    for w in range(4):
+        hist = np.bincount((outs[1][:, w] >> 24).astype(int), minlength=256)
+        assert sps.chisquare(hist).pvalue > 1e-3
+
+
+def test_philox_key_and_counter_sensitivity(orc):
+    base = orc.philox(np.array([[1, 2, 3, 4]]), SEED)[0]
+    flips = []
+    for word in range(4):
+        c = np.array([[1, 2, 3, 4]], dtype=np.uint32)
+        c[0, word] ^= 1
+        o = orc.philox(c, SEED)[0]
+        flips.append(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(base, o)))
+    o = orc.philox(np.array([[1, 2, 3, 4]]), SEED ^ 1)[0]
+    flips.append(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(base, o)))
+    # avalanche: one flipped input bit changes about half of the 128 output bits
+    for f in flips:
+        assert 40 < f < 88
+
+
+# ----------------------------------------------------------------------------- diffusion operator
+def _state_from(orc, L, O, G, H, cell=None):
+    st = orc.State(L)
+    st.O[:], st.G[:], st.H[:] = O, G, H
+    if cell is not None:
+        st.cell[:] = cell
+    return st
+
+
+@pytest.mark.parametrize("bc", [1, 2])  # periodic, no-flux
+def test_diffusion_conserves_mass(orc, bc):
+    L = 10
+    rng = np.random.default_rng(1)
+    O, G, H = rng.uniform(0.1, 0.3, L ** 3), rng.uniform(1, 5, L ** 3), rng.uniform(1e-5, 1e-4, L ** 3)
+    st = _state_from(orc, L, O, G, H)
+    p = P0.replace(flags=F_DEFAULT & ~F_DIVISION)
+    for s in range(5):
+        orc.step(p, st, SEED, 0, s, bc=bc)
+    for a, b in ((st.O, O), (st.G, G), (st.H, H)):
+        assert abs(a.sum() - b.sum()) <= 1e-12 * b.sum()
+        assert not np.allclose(a, b)  # something did diffuse
+
+
+@pytest.mark.parametrize("kvec", [(1, 0, 0), (0, 2, 1), (3, 1, 2)])
+def test_fourier_mode_decays_at_closed_form_rate(orc, kvec):
+    """Periodic lattice, no cells: c = A + B cos(2 pi k.x / L) is an eigenvector
+    of the 7-point FTCS substep with factor g = 1 - 4 lam sum_d sin^2(pi k_d / L)."""
+    L = 12
+    x, y, z = _coords(L)
+    ks = [kvec, (kvec[1], kvec[2], kvec[0]), (kvec[2], kvec[0], kvec[1])]  # a different mode per field
+    amp = [(0.2, 0.05), (3.0, 1.0), (5e-5, 2e-5)]
+    fields = []
+    for (kx, ky, kz), (A, B) in zip(ks, amp):
+        fields.append(A + B * np.cos(2 * np.pi * (kx * x + ky * y + kz * z) / L))
+    st = _state_from(orc, L, *fields)
+    orc.step(P0, st, SEED, 0, 0, bc=1)
+    for f, (kx, ky, kz), (A, B), lam in zip((st.O, st.G, st.H), ks, amp, P0.lam):
+        g = 1 - 4 * lam * sum(math.sin(math.pi * k / L) ** 2 for k in (kx, ky, kz))
+        want = A + B * g ** P0.n_sub * np.cos(2 * np.pi * (kx * x + ky * y + kz * z) / L)
+        np.testing.assert_allclose(f, want, rtol=0, atol=1e-13 * A)
+
+
+def test_dirichlet_mode_decays_at_closed_form_rate(orc):
+    """Faces held at the medium value A; c = A + B prod_d sin(pi k_d x_d/(L-1))
+    decays with g = 1 - 4 lam sum_d sin^2(pi k_d / (2 (L-1)))."""
+    L = 11
+    x, y, z = _coords(L)
+    k = (1, 2, 1)
+    mode = np.sin(np.pi * k[0] * x / (L - 1)) * np.sin(np.pi * k[1] * y / (L - 1)) * np.sin(np.pi * k[2] * z / (L - 1))
+    A = (P0.medium_O, P0.medium_G, 10 ** (3 - P0.medium_pH))
+    B = (0.1, 1.0, 1e-5)
+    st = _state_from(orc, L, *(a + b * mode for a, b in zip(A, B)))
+    orc.step(P0, st, SEED, 0, 0, bc=0)
+    for f, a, b, lam in zip((st.O, st.G, st.H), A, B, P0.lam):
+        g = 1 - 4 * lam * sum(math.sin(math.pi * kd / (2 * (L - 1))) ** 2 for kd in k)
+        np.testing.assert_allclose(f, a + b * g ** P0.n_sub * mode, rtol=0, atol=1e-13 * a)
+
+
+def test_medium_is_a_fixed_point(orc):
+    st = orc.init(P0, 12, -1, SEED)
+    ref = st.copy()
+    for s in range(3):
+        orc.step(P0, st, SEED, 0, s)
+    assert np.array_equal(st.O, ref.O) and np.array_equal(st.G, ref.G) and np.array_equal(st.H, ref.H)
+    assert st.O[0] == P0.medium_O and st.G[0] == P0.medium_G
+    assert math.isclose(st.H[0], 10 ** (3 - P0.medium_pH), rel_tol=1e-15)  # pH 7.4 -> 3.98e-5 mM
+
+
+# ----------------------------------------------------------------------------- reaction terms
+def _single_cell(orc, kind, O, G, H, n_sub=1):
+    L = 5
+    p = P0.replace(n_sub=n_sub, flags=F_REACTION)  # no diffusion, no cell events
+    st = _state_from(orc, L, np.full(L ** 3, O), np.full(L ** 3, G), np.full(L ** 3, H))
+    c = 2 + 5 * (2 + 5 * 2)
+    st.cell[c] = kind
+    orc.step(p, st, SEED, 0, 0)
+    return st, c
+
+
+def test_reaction_half_saturation_values(orc):
+    p = P0
+    # O2 uptake at O = K_O is half the maximum
+    st, c = _single_cell(orc, G1, p.K_O, 1.0, 1e-4)
+    assert math.isclose(st.O[c], p.K_O - p.q_O / 2, rel_tol=1e-14)
+    other = np.delete(np.arange(125), c)
+    assert np.all(st.O[other] == p.K_O)  # no cell, no uptake
+    # at O = O_an the anaerobic weight is 1/2; at G = K_G glucose uptake is half maximal
+    st, c = _single_cell(orc, S, p.O_an, p.K_G, 1e-4)
+    g = p.q_G / 2
+    assert math.isclose(p.K_G - st.G[c], g * (1 + (p.k_an - 1) / 2), rel_tol=1e-12)
+    assert math.isclose(st.H[c] - 1e-4, p.q_H * g * p.k_an / 2, rel_tol=1e-9)
+
+
+def test_reaction_limits_and_classes(orc):
+    p = P0
+    # anoxia: glucose uptake boosted by k_an, H+ released = q_H * anaerobic uptake
+    st, c = _single_cell(orc, G2, 0.0, p.K_G, 1e-4)
+    g = p.q_G / 2
+    assert st.O[c] == 0.0
+    assert math.isclose(p.K_G - st.G[c], g * p.k_an, rel_tol=1e-12)
+    assert math.isclose(st.H[c] - 1e-4, p.q_H * g * p.k_an, rel_tol=1e-9)
+    # oxygen-rich: no H+ release to first order, uptake close to aerobic
+    st, c = _single_cell(orc, M, 1e6, p.K_G, 1e-4)
+    assert abs(st.H[c] - 1e-4) < 1e-12
+    # quiescent cells take up f_Q of a cycling cell; empty sites nothing
+    st1, c = _single_cell(orc, G1, 0.1, 2.0, 1e-4)
+    stq, _ = _single_cell(orc, Q, 0.1, 2.0, 1e-4)
+    ste, _ = _single_cell(orc, EMPTY, 0.1, 2.0, 1e-4)
+    for a1, aq, ae, c0 in ((st1.O, stq.O, ste.O, 0.1), (st1.G, stq.G, ste.G, 2.0)):
+        assert math.isclose(c0 - aq[c], p.f_Q * (c0 - a1[c]), rel_tol=1e-12)
+        assert ae[c] == c0
+    # a field cannot go negative: uptake larger than the content clamps at zero
+    st, c = _single_cell(orc, G1, 1e-6, 1e-7, 1e-4, n_sub=4)
+    assert st.O[c] >= 0.0 and st.G[c] >= 0.0
+
+
+def test_reaction_mass_balance_noflux(orc):
+    """No-flux faces: the field total changes by exactly the summed uptake,
+    diffusion moves mass without creating it."""
+    L = 8
+    rng = np.random.default_rng(2)
+    p = P0.replace(n_sub=1, flags=F_REACTION | F_DIFFUSION)
+    O, G, H = rng.uniform(0.1, 0.3, L ** 3), rng.uniform(1, 5, L ** 3), rng.uniform(1e-5, 1e-4, L ** 3)
+    cell = rng.choice([EMPTY, G1, Q], size=L ** 3).astype(np.uint32)
+    st = _state_from(orc, L, O, G, H, cell)
+    lone = _state_from(orc, L, O, G, H, cell)
+    orc.step(p, st, SEED, 0, 0, bc=2)
+    orc.step(p.replace(flags=F_REACTION), lone, SEED, 0, 0, bc=2)  # same uptake without diffusion
+    for a, b, c0 in ((st.O, lone.O, O), (st.G, lone.G, G), (st.H, lone.H, H)):
+        assert abs((a.sum() - c0.sum()) - (b.sum() - c0.sum())) <= 1e-12 * c0.sum()
+    assert st.O.sum() < O.sum() and st.G.sum() < G.sum() and st.H.sum() > H.sum()
+
+
+# ----------------------------------------------------------------------------- irradiation
+def _lq_survival(p, kind, O, D):
+    omf = (p.omf_m * O + p.omf_K) / (p.omf_m * (O + p.omf_K))
+    mod = p.phi[kind - 1] * omf
+    return math.exp(-p.alpha * mod * D - p.beta * mod * mod * D * D)
+
+
+@pytest.mark.parametrize("kind,O,D", [(G1, 0.28, 2.0), (S, 0.28, 2.0), (G2, 0.28, 2.0), (M, 0.28, 2.0),
+                                      (Q, 0.28, 2.0), (G1, 0.0, 2.0), (G1, 4e-3, 5.0), (G2, 0.05, 1.25)])
+def test_lq_survival_inside_binomial_ci(orc, kind, O, D):
+    L = 48
+    p = P0.replace(flags=0)  # only irradiation acts; cells keep ageing
+    n = L ** 3
+    st = _state_from(orc, L, np.full(n, O), np.full(n, 5.5), np.full(n, 4e-5))
+    x, y, z = _coords(L)
+    interior = (x > 0) & (y > 0) & (z > 0) & (x < L - 1) & (y < L - 1) & (z < L - 1)
+    st.cell[interior] = kind
+    N = int(interior.sum())
+    _, stats = orc.step(p, st, SEED, 3, 11, dose=D)
+    doomed = int(np.count_nonzero(st.cell & 8))
+    S_ = _lq_survival(p, kind, O, D)
+    pk = 1 - S_
+    half = 3.29 * math.sqrt(pk * (1 - pk) / N)  # 99.9 % two-sided
+    assert abs(doomed / N - pk) <= half, (doomed / N, pk, half)
+    assert stats["n_doomed_new"] == doomed and stats["n_decisions"] == N
+    # the oxygen modifier: anoxic cells are hit 1/m as hard per Gy (alpha part)
+    if O == 0.0:
+        assert math.isclose(-math.log(S_), p.alpha * p.phi[0] / p.omf_m * D + p.beta * (p.phi[0] / p.omf_m * D) ** 2)
+
+
+def test_doomed_cells_die_at_mitosis(orc):
+    """A lethally hit cell keeps cycling and dies when it completes M."""
+    L = 6
+    p = P0.replace(dur_h=(1 / 600, 1 / 600, 1 / 600, 2 / 600), flags=F_DIVISION)
+    n = L ** 3
+    st = _state_from(orc, L, np.full(n, 0.28), np.full(n, 5.5), np.full(n, 4e-5))
+    c = 3 + 6 * (3 + 6 * 3)
+    st.cell[c] = S | 8  # DOOMED, S phase age 0
+    seen = []
+    for s in range(6):
+        orc.step(p, st, SEED, 0, s)
+        seen.append(int(st.cell[c]))
+    # S -> G2 -> M(0) -> M(1) -> dies at the end of M; nothing was placed
+    assert seen[:4] == [G2 | 8, M | 8, M | 8 | (1 << 4), EMPTY]
+    assert np.count_nonzero(st.cell) == 0
+
+
+# ----------------------------------------------------------------------------- cell cycle
+def test_cell_cycle_conveyor(orc):
+    """Division, death and quiescence off: every cell moves along the cycle as a
+    deterministic conveyor.  Position p = offset(kind) + age advances by one per
+    step and stops at the end of M."""
+    L = 14
+    p = P0.replace(dur_h=(40 / 600, 25 / 600, 15 / 600, 10 / 600), flags=F_REACTION | F_DIFFUSION)
+    st = orc.init(p, L, 5, SEED)
+    dur = [40, 25, 15, 10]
+    off = np.cumsum([0] + dur)
+    live = (st.cell & 7) != 0
+    kind0 = (st.cell & 7).astype(int)
+    age0 = (st.cell >> 4).astype(int)
+    pos0 = np.where(live, off[np.clip(kind0 - 1, 0, 3)] + age0, -1)
+    n0 = st.n_live()
+    T = 70
+    for s in range(T):
+        orc.step(p, st, SEED, 0, s)
+    assert st.n_live() == n0
+    pos = np.minimum(pos0 + T, off[4])
+    want_kind = np.where(pos >= off[4], M, np.searchsorted(off, pos, side="right"))
+    want_age = np.where(pos >= off[4], dur[3], pos - off[np.clip(want_kind - 1, 0, 3)])
+    kind = (st.cell & 7).astype(int)
+    age = (st.cell >> 4).astype(int)
+    assert np.array_equal(kind[live], want_kind[live])
+    assert np.array_equal(age[live], want_age[live])
+
+
+def test_init_ball_counts_and_uniform_phases(orc):
+    st = orc.init(P0, 40, 5, SEED)
+    assert st.n_live() == 515
+    st = orc.init(P0, 64, 8, SEED)
+    assert st.n_live() == 2109
+    kinds = np.bincount(st.cell & 7, minlength=6)[1:5]
+    assert sps.chisquare(kinds).pvalue > 1e-3
+    dur = [int(h * 600) for h in P0.dur_h]
+    age = st.cell >> 4
+    for k in range(1, 5):
+        a = age[(st.cell & 7) == k]
+        assert a.max() < dur[k - 1] and a.min() >= 0
+        assert sps.kstest(a / dur[k - 1], "uniform").pvalue > 1e-3
+    # no cell on a face; the same seed gives the same spheroid
+    x, y, z = _coords(64)
+    face = (x == 0) | (y == 0) | (z == 0) | (x == 63) | (y == 63) | (z == 63)
+    assert not np.any(st.cell[face])
+    assert np.array_equal(orc.init(P0, 64, 8, SEED).cell, st.cell)
+
+
+# ----------------------------------------------------------------------------- death & quiescence
+def test_thresholds_change_state_as_stated(orc):
+    L = 7
+    p = P0.replace(n_sub=1, flags=F_DEATH | F_QUIESCENCE)
+    n = L ** 3
+    Hq, Hd = 10 ** (3 - p.pH_q), 10 ** (3 - p.pH_d)
+    cases = [  # (kind, O, G, H) -> expected kind
+        (G1, 0.2, 5.0, 4e-5, G1),
+        (G1, 0.5 * p.O_q, 5.0, 4e-5, Q),        # hypoxia -> quiescent
+        (G1, 0.2, 0.5 * p.G_q + 0.5 * p.G_d, 4e-5, Q),
+        (G1, 0.2, 5.0, 0.5 * (Hq + Hd), Q),     # acidity between the two thresholds
+        (S, 0.5 * p.O_q, 5.0, 4e-5, S),          # only G1 cells become quiescent
+        (Q, 0.2, 5.0, 4e-5, G1),                 # conditions restored -> back to G1
+        (Q, 0.5 * p.O_q, 5.0, 4e-5, Q),
+        (M, 0.2, 0.5 * p.G_d, 4e-5, EMPTY),      # starvation -> necrosis
+        (Q, 0.2, 5.0, 1.5 * Hd, EMPTY),          # acid -> necrosis
+    ]
+    for kind, O, G, H, want in cases:
+        st = _state_from(orc, L, np.full(n, O), np.full(n, G), np.full(n, H))
+        c = 3 + 7 * (3 + 7 * 3)
+        st.cell[c] = kind | (5 << 4)
+        orc.step(p, st, SEED, 0, 0)
+        assert int(st.cell[c] & 7) == want, (kind, O, G, H, want, st.cell[c])
+
+
+# ----------------------------------------------------------------------------- division
+def _moore(L, s):
+    x, y, z = s % L, (s // L) % L, s // (L * L)
+    out = []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dx == dy == dz == 0:
+                    continue
+                out.append((x + dx) + L * ((y + dy) + L * (z + dz)))
+    return out
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_division_brute_force(orc, seed):
+    """8^3 lattice crowded with cells at the end of M: an independent slow
+    enumeration of every claim reproduces the oracle's placements, the count
+    rises by the number of winners and no site is taken twice."""
+    L = 8
+    rng = np.random.default_rng(seed)
+    p = P0.replace(flags=F_DIVISION)
+    durM = int(P0.dur_h[3] * 600)
+    n = L ** 3
+    x, y, z = _coords(L)
+    interior = (x > 0) & (y > 0) & (z > 0) & (x < L - 1) & (y < L - 1) & (z < L - 1)
+    cell = np.zeros(n, dtype=np.uint32)
+    r = rng.random(n)
+    cell[interior & (r < 0.35)] = M | ((durM - 1) << 4)  # completes M this step
+    cell[interior & (r >= 0.35) & (r < 0.5)] = G1 | (7 << 4)
+    st = _state_from(orc, L, np.full(n, 0.28), np.full(n, 5.5), np.full(n, 4e-5), cell)
+    before = st.cell.copy()
+    step = 17
+    orc.step(p, st, seed, 5, step)
+    # --- independent enumeration
+    after_update = before.copy()
+    parents = [s for s in range(n) if (before[s] & 7) == M]
+    for s in parents:
+        after_update[s] = M | (durM << 4)
+    for s in range(n):
+        if (before[s] & 7) == G1:
+            after_update[s] = before[s] + (1 << 4)
+    claims = {}
+    choice = {}
+    for s in parents:
+        free = [t for t in _moore(L, s) if interior[t] and (after_update[t] & 7) == EMPTY]
+        if not free:
+            continue
+        u = int(orc.philox(np.array([[s, step, 2, 5]]), seed)[0, 0])
+        t = free[((u >> 8) * len(free)) >> 24]
+        choice[s] = t
+        claims.setdefault(t, []).append(s)
+    want = after_update.copy()
+    winners = 0
+    for t, cl in claims.items():
+        w = min(cl)
+        want[w] = G1
+        want[t] = G1
+        winners += 1
+    assert winners > 0 and any(len(c) > 1 for c in claims.values())  # the case has real conflicts
+    assert np.array_equal(st.cell, want)
+    assert st.n_live() == int(np.count_nonzero(before & 7)) + winners
+    assert not np.any(st.cell[~interior])
+
+
+def test_division_off_keeps_count(orc):
+    p = P0.replace(flags=F_DEFAULT & ~F_DIVISION & ~F_DEATH)
+    st = orc.init(p, 20, 6, SEED)
+    n0 = st.n_live()
+    for s in range(1200):
+        orc.step(p, st, SEED, 0, s)
+    assert st.n_live() == n0
+
+
+# ----------------------------------------------------------------------------- brute force step on 8^3
+def _slow_step(p, L, O, G, H, cell, seed, protocol, step, dose, philox):
+    """Second, deliberately naive restatement of one Dirichlet step in pure Python."""
+    n = L ** 3
+    idx = lambda x, y, z: x + L * (y + L * z)
+    face = lambda x, y, z: min(x, y, z) == 0 or max(x, y, z) == L - 1
+    cell = list(int(c) for c in cell)
+    dur = [int(round(h * 600)) for h in p.dur_h]
+    Hm, Hq, Hd = 10 ** (3 - p.medium_pH), 10 ** (3 - p.pH_q), 10 ** (3 - p.pH_d)
+    if dose > 0:
+        for s in range(n):
+            k = cell[s] & 7
+            if k == 0:
+                continue
+            omf = (p.omf_m * O[s] + p.omf_K) / (p.omf_m * (O[s] + p.omf_K))
+            a, b = p.alpha * p.phi[k - 1] * omf, p.beta * (p.phi[k - 1] * omf) ** 2
+            u = (int(philox(np.array([[s, step, 1, protocol]]), seed)[0, 0]) >> 8) / 2 ** 24
+            if u >= math.exp(-a * dose - b * dose * dose):
+                cell[s] |= 8
+    F = [list(O), list(G), list(H)]
+    for _ in range(p.n_sub):
+        N = [f[:] for f in F]
+        for z in range(L):
+            for y in range(L):
+                for x in range(L):
+                    if face(x, y, z):
+                        continue
+                    s = idx(x, y, z)
+                    lap = []
+                    for f in F:
+                        nbrs = f[idx(x - 1, y, z)] + f[idx(x + 1, y, z)] + f[idx(x, y - 1, z)] + \
+                            f[idx(x, y + 1, z)] + f[idx(x, y, z - 1)] + f[idx(x, y, z + 1)]
+                        lap.append(nbrs - 6 * f[s])
+                    k = cell[s] & 7
+                    uO = uG = pH = 0.0
+                    if k:
+                        fw = p.f_Q if k == Q else 1.0
+                        o, g = F[0][s], F[1][s]
+                        uO = fw * p.q_O * o / (o + p.K_O)
+                        gg = fw * p.q_G * g / (g + p.K_G)
+                        w = p.O_an / (o + p.O_an)
+                        uG = gg * (1 + (p.k_an - 1) * w)
+                        pH = p.q_H * gg * p.k_an * w
+                    N[0][s] = max(F[0][s] + p.lam[0] * lap[0] - uO, 0.0)
+                    N[1][s] = max(F[1][s] + p.lam[1] * lap[1] - uG, 0.0)
+                    N[2][s] = max(F[2][s] + p.lam[2] * lap[2] + pH, 0.0)
+        F = N
+    nxt = cell[:]
+    for s in range(n):
+        w = cell[s]
+        k, dm, age = w & 7, w & 8, w >> 4
+        if k == 0:
+            continue
+        o, g, h = F[0][s], F[1][s], F[2][s]
+        if g < p.G_d or h > Hd:
+            nxt[s] = 0
+            continue
+        bad = o < p.O_q or g < p.G_q or h > Hq
+        if k == Q:
+            if not bad:
+                nxt[s] = G1 | dm
+            continue
+        if k == G1 and bad:
+            nxt[s] = Q | dm
+            continue
+        age += 1
+        if age >= dur[k - 1]:
+            if k < M:
+                k, age = k + 1, 0
+            elif dm:
+                nxt[s] = 0
+                continue
+            else:
+                age = dur[3]
+        nxt[s] = k | dm | (age << 4)
+    cell = nxt
+    claims, tgt = {}, {}
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                s = idx(x, y, z)
+                if (cell[s] & 7) != M or (cell[s] & 8) or (cell[s] >> 4) != dur[3]:
+                    continue
+                free = []
+                for dz in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            if dx == dy == dz == 0 or face(x + dx, y + dy, z + dz):
+                                continue
+                            t = idx(x + dx, y + dy, z + dz)
+                            if (cell[t] & 7) == 0:
+                                free.append(t)
+                if free:
+                    u = int(philox(np.array([[s, step, 2, protocol]]), seed)[0, 0])
+                    tgt[s] = free[((u >> 8) * len(free)) >> 24]
+                    claims[tgt[s]] = min(claims.get(tgt[s], s), s)
+    for s, t in tgt.items():
+        if claims[t] == s:
+            cell[s] = G1
+            cell[t] = G1
+    return np.array(F[0]), np.array(F[1]), np.array(F[2]), np.array(cell, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("seed,dose", [(11, 0.0), (12, 3.0)])
+def test_step_matches_naive_restatement_8cube(orc, seed, dose):
+    L = 8
+    rng = np.random.default_rng(seed)
+    durs = [int(round(h * 600)) for h in P0.dur_h]
+    n = L ** 3
+    x, y, z = _coords(L)
+    interior = (x > 0) & (y > 0) & (z > 0) & (x < L - 1) & (y < L - 1) & (z < L - 1)
+    kind = rng.integers(0, 6, n)
+    kind[~interior] = 0
+    age = np.array([rng.integers(0, durs[k - 1]) if 1 <= k <= 4 else 0 for k in kind])
+    age[(kind == M) & (rng.random(n) < 0.5)] = durs[3] - 1
+    cell = (kind | (age << 4) | ((rng.random(n) < 0.1) * 8 * (kind > 0))).astype(np.uint32)
+    Hm = 10 ** (3 - P0.medium_pH)
+    O = np.where(interior, rng.uniform(0.0, 0.3, n), P0.medium_O)
+    G = np.where(interior, rng.uniform(0.0, 5.5, n), P0.medium_G)
+    H = np.where(interior, rng.uniform(Hm, 5e-4, n), Hm)
+    st = _state_from(orc, L, O, G, H, cell)
+    orc.step(P0, st, seed, 9, 123, dose=dose)
+    wO, wG, wH, wc = _slow_step(P0, L, O, G, H, cell, seed, 9, 123, dose, orc.philox)
+    np.testing.assert_allclose(st.O, wO, rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(st.G, wG, rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(st.H, wH, rtol=1e-13, atol=1e-20)
+    assert np.array_equal(st.cell, wc)
+
+
+# ----------------------------------------------------------------------------- protocol semantics
+def test_protocol_schedule_matches_paper_benchmarks(orc):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "benchmark_protocols.json")) as f:
+        gold = json.load(f)
+    for name, entry in gold["protocols"].items():
+        doses = [d for d, _ in entry["pairs"]]
+        waits = [w for _, w in entry["pairs"]]
+        assert sum(doses) <= gold["total_dose_cap_gy"] + 1e-12
+        assert list(orc.fraction_steps(waits)) == entry["fraction_steps"], name
+
+
+def test_run_applies_fractions_and_counts(orc):
+    """A whole run: hourly counts start at the seeded size, the delivered dose
+    equals the protocol's total, and a large dose lowers the final count."""
+    L, R = 14, 3
+    ctrl = orc.run(P0, L, R, SEED, 0, [], [], t_end_steps=1800, hours=3)
+    hit = orc.run(P0, L, R, SEED, 0, [8.0], [0.0], t_end_steps=1800, hours=3)
+    assert ctrl["counts"][0] == hit["counts"][0] == 123  # lattice points with |r|^2 <= 9
+    assert hit["cum_dose"] == 8.0 and ctrl["cum_dose"] == 0.0
+    assert ctrl["steps"] == 1800 and np.all(ctrl["counts"] >= 0)
+    assert hit["stats"]["n_doomed_new"] > 0
