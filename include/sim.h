@@ -1,0 +1,162 @@
+/*
+ * sim.h -- C ABI of the batched EMT6/Ro spheroid simulator (libsim).
+ *
+ * Computes, for a batch of radiotherapy protocols, the time-stepped cellular
+ * automaton of an EMT6/Ro tumour spheroid (arxiv 2303.08123, "Underlying model"):
+ * reaction-diffusion of oxygen, glucose and H+ with per-cell metabolism,
+ * cell-cycle progression, death, division into free neighbouring sites and the
+ * irradiation kill at each dose fraction, on a cubic lattice with 600 steps per
+ * simulated hour ("GA Resolution, constraints").  A protocol is a list of
+ * (dose Gy, wait h) pairs whose first wait counts from t = 0 ("Defining the
+ * search problem"); the output is the live-cell count over time and the
+ * fitness f = n_max - n at the end of the run (Eq. final_fit_fun).
+ *
+ * Conventions
+ *  - Every call returns sim_status; nothing is thrown across the ABI.
+ *  - The caller owns every buffer.  Host pointers are borrowed for the call.
+ *    The device workspace given to sim_create is borrowed for the context's
+ *    lifetime; the library never allocates device memory.
+ *  - Work is enqueued on the CUDA stream given to sim_create.  Calls marked
+ *    "synchronises" wait for that stream and report device-side errors.
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - Lattice site index s = x + L*(y + L*z); sites with a coordinate equal to
+ *    0 or L-1 are faces that hold the medium values and never hold cells.
+ *  - Cell word: bits 0..2 kind (0 empty, 1 G1, 2 S, 3 G2, 4 M, 5 quiescent),
+ *    bit 3 DOOMED (lethally irradiated), bits 4..31 age in steps in the phase.
+ */
+#ifndef GPUGA_SIM_H
+#define GPUGA_SIM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = -1,   /* bad argument or protocol (message in sim_last_error) */
+    SIM_ENOSPC = -2,   /* workspace or host buffer too small */
+    SIM_ECUDA = -3,    /* a CUDA call failed */
+    SIM_ETIMEOUT = -4, /* a bounded device wait ran out */
+    SIM_ESTATE = -5    /* call not valid in the context's current state */
+} sim_status;
+
+enum { SIM_FP32 = 0, SIM_BF16 = 1, SIM_FP16 = 2 };         /* field storage precision */
+enum { SIM_F_DIVISION = 1, SIM_F_DEATH = 2, SIM_F_QUIESCENCE = 4, SIM_F_REACTION = 8,
+       SIM_F_DIFFUSION = 16, SIM_F_DOOM_IMMEDIATE = 32 };  /* model switches */
+
+/* Model parameters (host doubles; the library converts them to FP32). */
+typedef struct {
+    double dur_h[4];      /* phase durations G1, S, G2, M in hours (600 steps per hour) */
+    int32_t n_sub;        /* explicit diffusion substeps per CA step */
+    int32_t flags;        /* SIM_F_* */
+    double lam[3];        /* per-substep diffusion numbers for O2, glucose, H+ (<= 1/6) */
+    double medium_O, medium_G, medium_pH; /* medium: mM, mM, pH */
+    double q_O, K_O, q_G, K_G, k_an, O_an, q_H, f_Q; /* metabolism (mM per substep) */
+    double alpha, beta, omf_m, omf_K;     /* LQ survival and oxygen modification */
+    double phi[5];        /* radiosensitivity factors G1, S, G2, M, quiescent */
+    double O_q, G_q, pH_q, G_d, pH_d;     /* quiescence and death thresholds */
+} sim_params;
+
+typedef struct {
+    sim_params params;
+    uint64_t seed;          /* Philox key */
+    int32_t precision;      /* SIM_FP32 / SIM_BF16 / SIM_FP16 field storage */
+    int32_t regrowth_h;     /* horizon = last fraction + regrowth_h (paper: 5 days) */
+    int64_t t_end_steps;    /* > 0: fixed horizon for every protocol instead */
+    double n_max_fitness;   /* fitness = n_max - n (paper: 1500) */
+    double dose_cap_gy;     /* reject protocols whose total dose exceeds this */
+    int32_t hours;          /* hourly counts kept per protocol for hours 0..hours */
+    int32_t max_fractions;  /* capacity of each protocol's fraction table */
+    uint32_t init_word;     /* Philox protocol word of the seeded spheroid */
+    int32_t use_graphs;     /* 1: replay each simulated hour as one CUDA graph */
+} sim_config;
+
+typedef struct sim_ctx sim_ctx;
+
+/*
+ * Device workspace needed for n protocols on lattices L[0..n-1] (each 8..1024).
+ * Fields are stored double-buffered in the configured precision; per site the
+ * workspace holds 2 x 3 field values, a 4-byte cell word, an 8-byte division
+ * claim and 8 bytes of division work list.  Errors: SIM_EINVAL on NULL or
+ * out-of-range arguments.
+ */
+sim_status sim_workspace_size(const sim_config* cfg, int n, const int32_t* L, size_t* bytes);
+
+/*
+ * Create a context over a caller-allocated device workspace (at least
+ * sim_workspace_size bytes, 256-byte aligned) and a CUDA stream (NULL = the
+ * legacy default stream).  L and R (host, n entries) give each protocol's
+ * lattice size and initial spheroid radius (R < 0: empty lattice).  Seeds every
+ * spheroid (asynchronously).  *out receives the context.
+ * Errors: SIM_EINVAL, SIM_ENOSPC (workspace too small), SIM_ECUDA.
+ */
+sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int32_t* R, void* d_workspace,
+                      size_t bytes, void* cuda_stream, sim_ctx** out);
+
+/*
+ * Load one protocol per slot (host CSR: offsets[n+1], dose_gy[], wait_h[]) and
+ * reset every slot to its seeded spheroid at step 0.  n must equal the
+ * context's protocol count.  Fraction j of a protocol fires at step
+ * round(600 * sum_{i<=j} wait_i); doses landing on one step add up.
+ * Rejected (SIM_EINVAL): negative dose or wait, a wait not on the 30 min grid,
+ * total dose above dose_cap_gy, more than max_fractions fractions.
+ */
+sim_status sim_load_protocols(sim_ctx* ctx, int n, const int32_t* offsets, const double* dose_gy,
+                              const double* wait_h);
+
+/* Re-seed every spheroid and set the clock to step 0 (asynchronous). */
+sim_status sim_reset(sim_ctx* ctx);
+
+/*
+ * Advance every protocol by up to max_steps steps (max_steps <= 0: until every
+ * protocol reaches its horizon).  A protocol past its horizon stays frozen.
+ * Asynchronous; device errors surface at the next synchronising call.
+ */
+sim_status sim_run(sim_ctx* ctx, int64_t max_steps);
+
+/* Final live count n and fitness n_max - n per protocol (host outputs, n
+ * entries each; either may be NULL).  Synchronises. */
+sim_status sim_fitness(sim_ctx* ctx, int32_t* out_count, double* out_fitness);
+
+/* Hourly live counts (host, n x (hours+1), row-major; -1 where the hour lies
+ * beyond the protocol's horizon or has not been reached).  Synchronises. */
+sim_status sim_counts(sim_ctx* ctx, int32_t* out, int hours);
+
+/* Delivered dose per protocol in Gy (host, n entries, FP64).  Synchronises. */
+sim_status sim_delivered_dose(sim_ctx* ctx, double* out);
+
+/* Current step and horizon of every protocol (host, n entries; either may be
+ * NULL). */
+sim_status sim_clock(sim_ctx* ctx, int64_t* step, int64_t* t_end);
+
+/* Set the step counter of every protocol (parity tests start a step at a
+ * chosen Philox step index). */
+sim_status sim_set_clock(sim_ctx* ctx, int64_t step);
+
+/* Copy protocol p's lattice to / from host arrays (FP32 fields in mM, L^3
+ * each, converted from / to the storage precision; cell words).  Any pointer
+ * may be NULL to skip that array.  Synchronises. */
+sim_status sim_get_state(sim_ctx* ctx, int p, float* O, float* G, float* H, uint32_t* cell);
+sim_status sim_set_state(sim_ctx* ctx, int p, const float* O, const float* G, const float* H,
+                         const uint32_t* cell);
+
+/* Checkpoint the whole batch (fields, cells, clock, delivered dose, counts)
+ * into a host buffer; with buf == NULL only *bytes is set to the size needed.
+ * Philox is counter-based, so a restored run continues bit for bit.
+ * Synchronises.  SIM_ENOSPC if the buffer is too small. */
+sim_status sim_save_state(sim_ctx* ctx, void* buf, size_t* bytes);
+sim_status sim_load_state(sim_ctx* ctx, const void* buf, size_t bytes);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* sim_last_error(const sim_ctx* ctx);
+const char* sim_status_string(sim_status s);
+
+/* Release the context (the workspace stays the caller's).  NULL is a no-op. */
+void sim_destroy(sim_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,666 @@
+// sim_api.cu -- the C ABI of libsim (declared in include/sim.h).
+//
+// Host side of the batched simulator: validates protocols, lays the batch out
+// in the caller's workspace, builds the ragged work list, launches the step
+// kernels (or replays one captured CUDA graph per simulated hour) and moves
+// results back.  No device memory is allocated here.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sim.h"
+#include "sim_kernels.cuh"
+
+using namespace simdev;
+
+namespace {
+
+constexpr int kSitesPerBlock = 1024;  // work-list granularity (sites per CTA)
+constexpr int kMaxL = 1024;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t elem_size(int precision) { return precision == SIM_FP32 ? 4 : 2; }
+
+// Byte offsets of every region of the workspace.
+struct Layout {
+    size_t proto, blocks, fstep, fdose, field[2][3], cell, claim, intents, target, icount, counts, cum, clock,
+        status, final_count, total;
+};
+
+Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks) {
+    Layout l{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    const size_t es = elem_size(cfg.precision);
+    const int64_t nf = (int64_t)n * cfg.max_fractions;
+    l.proto = take(sizeof(Proto) * n);
+    l.blocks = take(sizeof(Block) * nblocks);
+    l.fstep = take(sizeof(int64_t) * (nf > 0 ? nf : 1));
+    l.fdose = take(sizeof(double) * (nf > 0 ? nf : 1));
+    for (int b = 0; b < 2; ++b)
+        for (int f = 0; f < 3; ++f) l.field[b][f] = take(es * total_sites);
+    l.cell = take(4 * total_sites);
+    l.claim = take(8 * total_sites);
+    l.intents = take(4 * total_sites);
+    l.target = take(4 * total_sites);
+    l.icount = take(4 * 2);
+    l.counts = take(sizeof(int32_t) * n * (size_t)(cfg.hours + 1));
+    l.cum = take(sizeof(double) * n);
+    l.clock = take(sizeof(int64_t));
+    l.status = take(sizeof(uint32_t));
+    l.final_count = take(sizeof(int32_t) * n);
+    l.total = off;
+    return l;
+}
+
+bool valid_config(const sim_config* cfg, std::string* why) {
+    const sim_params& p = cfg->params;
+    if (cfg->precision < SIM_FP32 || cfg->precision > SIM_FP16) return *why = "precision must be 0, 1 or 2", false;
+    if (p.n_sub < 1 || p.n_sub > 64) return *why = "n_sub must be in 1..64", false;
+    for (int i = 0; i < 4; ++i) {
+        const double st = p.dur_h[i] * kStepsPerHour;
+        if (!(st >= 1.0) || st > 1e8) return *why = "phase durations must be at least one step", false;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (!(p.lam[i] >= 0.0 && p.lam[i] <= 1.0 / 6.0 + 1e-12))
+            return *why = "diffusion numbers must lie in [0, 1/6] (FTCS stability in 3-D)", false;
+    if (cfg->hours < 0 || cfg->hours > 1000000) return *why = "hours out of range", false;
+    if (cfg->max_fractions < 0 || cfg->max_fractions > 100000) return *why = "max_fractions out of range", false;
+    if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
+    return true;
+}
+
+}  // namespace
+
+struct sim_ctx {
+    sim_config cfg{};
+    Params P{};
+    int n = 0;
+    std::vector<Proto> proto;
+    std::vector<Block> blocks;
+    int64_t total_sites = 0;
+    Layout lay{};
+    char* ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int64_t clock = 0;          // host mirror of the device clock
+    int cur = 0;                // field buffer holding the current state
+    int64_t counted_hour = -1;  // last hour whose counts were recorded
+    bool loaded = false;
+    cudaGraphExec_t hour_graph[2] = {nullptr, nullptr};  // indexed by the starting buffer
+    std::string err;
+
+    template <typename T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+    void* field(int buf, int f) const { return ws + lay.field[buf][f]; }
+};
+
+namespace {
+
+sim_status fail(sim_ctx* c, sim_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+sim_status cuda_check(sim_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SIM_OK;
+    return fail(c, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+Params make_params(const sim_config& cfg) {
+    const sim_params& p = cfg.params;
+    Params P{};
+    for (int i = 0; i < 4; ++i) P.dur[i] = (int)llround(p.dur_h[i] * kStepsPerHour);
+    P.n_sub = p.n_sub;
+    P.flags = p.flags;
+    for (int i = 0; i < 3; ++i) P.lam[i] = (float)p.lam[i];
+    P.med[0] = (float)p.medium_O;
+    P.med[1] = (float)p.medium_G;
+    P.med[2] = (float)std::pow(10.0, 3.0 - p.medium_pH);  // pH -> mM of H+
+    P.q_O = (float)p.q_O; P.K_O = (float)p.K_O; P.q_G = (float)p.q_G; P.K_G = (float)p.K_G;
+    P.k_an = (float)p.k_an; P.O_an = (float)p.O_an; P.q_H = (float)p.q_H; P.f_Q = (float)p.f_Q;
+    P.alpha = (float)p.alpha; P.beta = (float)p.beta; P.omf_m = (float)p.omf_m; P.omf_K = (float)p.omf_K;
+    for (int i = 0; i < 5; ++i) P.phi[i] = (float)p.phi[i];
+    P.O_q = (float)p.O_q; P.G_q = (float)p.G_q; P.G_d = (float)p.G_d;
+    P.H_q = (float)std::pow(10.0, 3.0 - p.pH_q);
+    P.H_d = (float)std::pow(10.0, 3.0 - p.pH_d);
+    P.key0 = (uint32_t)(cfg.seed & 0xffffffffu);
+    P.key1 = (uint32_t)(cfg.seed >> 32);
+    P.init_word = cfg.init_word;
+    return P;
+}
+
+template <typename T>
+sim_status launch_init(sim_ctx* c) {
+    k_init<T><<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
+        c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), (T*)c->field(0, 0), (T*)c->field(0, 1),
+        (T*)c->field(0, 2), (T*)c->field(1, 0), (T*)c->field(1, 1), (T*)c->field(1, 2), c->at<uint32_t>(c->lay.cell),
+        c->at<unsigned long long>(c->lay.claim), c->P);
+    return cuda_check(c, cudaGetLastError(), "k_init launch");
+}
+
+sim_status reset_device(sim_ctx* c) {
+    sim_status st;
+    switch (c->cfg.precision) {
+        case SIM_BF16: st = launch_init<__nv_bfloat16>(c); break;
+        case SIM_FP16: st = launch_init<__half>(c); break;
+        default: st = launch_init<float>(c); break;
+    }
+    if (st) return st;
+    cudaError_t e = cudaMemsetAsync(c->ws + c->lay.icount, 0, 8, c->stream);
+    if (!e)
+        e = cudaMemsetAsync(c->ws + c->lay.counts, 0, sizeof(int32_t) * c->n * (size_t)(c->cfg.hours + 1), c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.cum, 0, sizeof(double) * c->n, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.clock, 0, sizeof(int64_t), c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.status, 0, sizeof(uint32_t), c->stream);
+    c->clock = 0;
+    c->cur = 0;
+    c->counted_hour = -1;
+    return cuda_check(c, e, "reset");
+}
+
+// One CA step for every protocol, reading the step index as clock + k_off.
+template <typename T>
+sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf) {
+    const unsigned nb = (unsigned)c->blocks.size();
+    const Block* blocks = c->at<Block>(c->lay.blocks);
+    const Proto* protos = c->at<Proto>(c->lay.proto);
+    const int64_t* clock = c->at<int64_t>(c->lay.clock);
+    uint32_t* cell = c->at<uint32_t>(c->lay.cell);
+    int buf = start_buf;
+    for (int sub = 0; sub < c->P.n_sub; ++sub) {
+        k_substep<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, sub == 0, (const T*)c->field(buf, 0),
+                                             (const T*)c->field(buf, 1), (const T*)c->field(buf, 2),
+                                             (T*)c->field(buf ^ 1, 0), (T*)c->field(buf ^ 1, 1),
+                                             (T*)c->field(buf ^ 1, 2), cell, c->at<int64_t>(c->lay.fstep),
+                                             c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum), c->P);
+        buf ^= 1;
+    }
+    k_cell<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, (const T*)c->field(buf, 0),
+                                      (const T*)c->field(buf, 1), (const T*)c->field(buf, 2), cell,
+                                      c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->P);
+    // the work list is short (cells at the end of M): a fixed grid strides over it
+    const unsigned ng = 148 * 4;
+    k_claim<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
+                                    c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
+                                    c->at<unsigned long long>(c->lay.claim), c->P);
+    k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
+                                      c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
+                                      c->at<unsigned long long>(c->lay.claim));
+    return cuda_check(c, cudaGetLastError(), "step launch");
+}
+
+sim_status step_dispatch(sim_ctx* c, cudaStream_t s, int k_off, int start_buf) {
+    switch (c->cfg.precision) {
+        case SIM_BF16: return enqueue_step<__nv_bfloat16>(c, s, k_off, start_buf);
+        case SIM_FP16: return enqueue_step<__half>(c, s, k_off, start_buf);
+        default: return enqueue_step<float>(c, s, k_off, start_buf);
+    }
+}
+
+sim_status tick(sim_ctx* c, cudaStream_t s, int64_t by) {
+    k_tick<<<1, 1, 0, s>>>(c->at<int64_t>(c->lay.clock), by);
+    return cuda_check(c, cudaGetLastError(), "k_tick launch");
+}
+
+sim_status count_hour(sim_ctx* c) {
+    const int64_t h = c->clock / kStepsPerHour;
+    if (c->clock % kStepsPerHour != 0 || h > c->cfg.hours || h <= c->counted_hour) return SIM_OK;
+    k_count<<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
+        c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock),
+        c->at<uint32_t>(c->lay.cell), c->at<int32_t>(c->lay.counts), c->cfg.hours + 1, 1);
+    c->counted_hour = h;
+    return cuda_check(c, cudaGetLastError(), "k_count launch");
+}
+
+// Capture one simulated hour (600 steps + clock advance) starting from field
+// buffer `start` as a CUDA graph.  Captured on a private stream; replayed on
+// the context's stream.
+sim_status build_hour_graph(sim_ctx* c, int start) {
+    if (c->hour_graph[start]) return SIM_OK;
+    cudaError_t e = cudaSuccess;
+    if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+    if (e) return cuda_check(c, e, "capture stream");
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e) return cuda_check(c, e, "begin capture");
+    int buf = start;
+    sim_status st = SIM_OK;
+    for (int k = 0; k < kStepsPerHour && st == SIM_OK; ++k) {
+        st = step_dispatch(c, c->capture_stream, k, buf);
+        buf ^= (c->P.n_sub & 1);
+    }
+    if (st == SIM_OK) st = tick(c, c->capture_stream, kStepsPerHour);
+    e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e) return cuda_check(c, e, "end capture");
+    e = cudaGraphInstantiate(&c->hour_graph[start], g, 0);
+    cudaGraphDestroy(g);
+    return cuda_check(c, e, "graph instantiate");
+}
+
+void drop_graphs(sim_ctx* c) {
+    for (auto& g : c->hour_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+int64_t max_t_end(const sim_ctx* c) {
+    int64_t m = 0;
+    for (const Proto& p : c->proto) m = p.t_end > m ? p.t_end : m;
+    return m;
+}
+
+sim_status read_status(sim_ctx* c) {
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->ws + c->lay.status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_check(c, e, "synchronise");
+    if (st) return fail(c, SIM_ETIMEOUT, "device reported status " + std::to_string(st));
+    return SIM_OK;
+}
+
+template <typename T>
+void to_float(const void* src, float* dst, int64_t n) {
+    const T* s = (const T*)src;
+    for (int64_t i = 0; i < n; ++i) dst[i] = (float)s[i];
+}
+
+struct CkptHeader {
+    char magic[8];
+    int32_t n, precision;
+    int64_t total_sites, clock, counted_hour;
+    int32_t cur, hours;
+};
+
+size_t ckpt_bytes(const sim_ctx* c) {
+    const size_t es = elem_size(c->cfg.precision);
+    const size_t ncnt = (size_t)c->n * (c->cfg.hours + 1);
+    return sizeof(CkptHeader) + 3 * es * c->total_sites + 4 * c->total_sites + 8 * c->n + 4 * ncnt;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_status_string(sim_status s) {
+    switch (s) {
+        case SIM_OK: return "ok";
+        case SIM_EINVAL: return "invalid argument";
+        case SIM_ENOSPC: return "buffer too small";
+        case SIM_ECUDA: return "CUDA error";
+        case SIM_ETIMEOUT: return "device wait timed out";
+        case SIM_ESTATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* sim_last_error(const sim_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sim_status sim_workspace_size(const sim_config* cfg, int n, const int32_t* L, size_t* bytes) {
+    if (!cfg || !L || !bytes || n < 1) return SIM_EINVAL;
+    std::string why;
+    if (!valid_config(cfg, &why)) return SIM_EINVAL;
+    int64_t total = 0, nb = 0;
+    for (int p = 0; p < n; ++p) {
+        if (L[p] < 8 || L[p] > kMaxL) return SIM_EINVAL;
+        const int64_t sites = (int64_t)L[p] * L[p] * L[p];
+        total += sites;
+        nb += (sites + kSitesPerBlock - 1) / kSitesPerBlock;
+    }
+    if (total >= (int64_t)0xffffffffLL) return SIM_EINVAL;  // work list holds 32-bit site indices
+    *bytes = make_layout(*cfg, n, total, nb).total;
+    return SIM_OK;
+}
+
+sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int32_t* R, void* d_workspace,
+                      size_t bytes, void* cuda_stream, sim_ctx** out) {
+    if (!out) return SIM_EINVAL;
+    *out = nullptr;
+    if (!cfg || !L || !R || !d_workspace || n < 1) return SIM_EINVAL;
+    if (((uintptr_t)d_workspace) % kAlign) return SIM_EINVAL;
+    size_t need = 0;
+    if (sim_workspace_size(cfg, n, L, &need) != SIM_OK) return SIM_EINVAL;
+    if (bytes < need) return SIM_ENOSPC;
+    sim_ctx* c = new sim_ctx();
+    c->cfg = *cfg;
+    c->n = n;
+    c->P = make_params(*cfg);
+    c->ws = (char*)d_workspace;
+    c->stream = (cudaStream_t)cuda_stream;
+    int64_t site0 = 0;
+    for (int p = 0; p < n; ++p) {
+        Proto pr{};
+        pr.L = L[p];
+        pr.R = R[p];
+        pr.site0 = site0;
+        pr.t_end = 0;
+        pr.frac0 = p * cfg->max_fractions;
+        pr.nfrac = 0;
+        const int64_t sites = (int64_t)L[p] * L[p] * L[p];
+        for (int64_t b = 0; b < sites; b += kSitesPerBlock) {
+            Block bl{};
+            bl.p = p;
+            bl.begin = b;
+            bl.n = (int)((sites - b) < kSitesPerBlock ? (sites - b) : kSitesPerBlock);
+            c->blocks.push_back(bl);
+        }
+        site0 += sites;
+        c->proto.push_back(pr);
+    }
+    c->total_sites = site0;
+    c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size());
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.blocks, c->blocks.data(), sizeof(Block) * c->blocks.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (!e)
+        e = cudaMemcpyAsync(c->ws + c->lay.proto, c->proto.data(), sizeof(Proto) * n, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);  // host vectors may change before the copy would run
+    sim_status st = cuda_check(c, e, "create copies");
+    if (!st) st = reset_device(c);
+    if (st) {
+        delete c;
+        return st;
+    }
+    *out = c;
+    return SIM_OK;
+}
+
+sim_status sim_load_protocols(sim_ctx* c, int n, const int32_t* offsets, const double* dose_gy,
+                              const double* wait_h) {
+    if (!c) return SIM_EINVAL;
+    if (n != c->n || !offsets) return fail(c, SIM_EINVAL, "protocol count must equal the context's slots");
+    if (offsets[0] != 0) return fail(c, SIM_EINVAL, "offsets[0] must be 0");
+    const int F = c->cfg.max_fractions;
+    const size_t cap = (size_t)n * (F > 0 ? F : 1);
+    std::vector<int64_t> fstep(cap, -1);
+    std::vector<double> fdose(cap, 0.0);
+    std::vector<Proto> proto = c->proto;
+    for (int p = 0; p < n; ++p) {
+        const int a = offsets[p], b = offsets[p + 1];
+        if (b < a) return fail(c, SIM_EINVAL, "offsets must be non-decreasing");
+        if ((a != b) && (!dose_gy || !wait_h)) return fail(c, SIM_EINVAL, "dose/wait arrays missing");
+        double t_h = 0.0, total = 0.0;
+        int nf = 0;
+        int64_t last = -1;
+        for (int j = a; j < b; ++j) {
+            const double d = dose_gy[j], w = wait_h[j];
+            if (!std::isfinite(d) || !std::isfinite(w) || d < 0.0 || w < 0.0)
+                return fail(c, SIM_EINVAL, "protocol " + std::to_string(p) + ": negative or non-finite dose/wait");
+            if (std::fabs(w * 2.0 - std::round(w * 2.0)) > 1e-9)
+                return fail(c, SIM_EINVAL, "protocol " + std::to_string(p) + ": wait not on the 30 min grid");
+            t_h += w;
+            total += d;
+            const int64_t st = llround(kStepsPerHour * t_h);
+            last = st;
+            if (d == 0.0) continue;
+            if (nf > 0 && fstep[(size_t)p * F + nf - 1] == st) {  // fractions on one step add up
+                fdose[(size_t)p * F + nf - 1] += d;
+                continue;
+            }
+            if (nf >= F) return fail(c, SIM_EINVAL, "protocol " + std::to_string(p) + ": too many fractions");
+            fstep[(size_t)p * F + nf] = st;
+            fdose[(size_t)p * F + nf] = d;
+            ++nf;
+        }
+        if (total > c->cfg.dose_cap_gy + 1e-9)
+            return fail(c, SIM_EINVAL, "protocol " + std::to_string(p) + ": total dose above the cap");
+        proto[p].nfrac = nf;
+        proto[p].t_end = c->cfg.t_end_steps > 0
+                             ? c->cfg.t_end_steps
+                             : (last > 0 ? last : 0) + (int64_t)kStepsPerHour * c->cfg.regrowth_h;
+    }
+    cudaError_t e = cudaSuccess;
+    if (F > 0) {
+        e = cudaMemcpyAsync(c->ws + c->lay.fstep, fstep.data(), sizeof(int64_t) * cap, cudaMemcpyHostToDevice,
+                            c->stream);
+        if (!e)
+            e = cudaMemcpyAsync(c->ws + c->lay.fdose, fdose.data(), sizeof(double) * cap, cudaMemcpyHostToDevice,
+                                c->stream);
+    }
+    if (!e)
+        e = cudaMemcpyAsync(c->ws + c->lay.proto, proto.data(), sizeof(Proto) * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);  // the staging vectors die with this call
+    if (e) return cuda_check(c, e, "load protocols");
+    c->proto = proto;
+    c->loaded = true;
+    return reset_device(c);
+}
+
+sim_status sim_reset(sim_ctx* c) {
+    if (!c) return SIM_EINVAL;
+    return reset_device(c);
+}
+
+sim_status sim_run(sim_ctx* c, int64_t max_steps) {
+    if (!c) return SIM_EINVAL;
+    if (!c->loaded) return fail(c, SIM_ESTATE, "load protocols before running");
+    int64_t target = max_t_end(c);
+    if (max_steps > 0 && c->clock + max_steps < target) target = c->clock + max_steps;
+    const bool graphs = c->cfg.use_graphs != 0;
+    sim_status st = SIM_OK;
+    while (c->clock < target && st == SIM_OK) {
+        st = count_hour(c);
+        if (st) break;
+        if (graphs && c->clock % kStepsPerHour == 0 && c->clock + kStepsPerHour <= target) {
+            st = build_hour_graph(c, c->cur);
+            if (st) break;
+            cudaError_t e = cudaGraphLaunch(c->hour_graph[c->cur], c->stream);
+            if (e) return cuda_check(c, e, "graph launch");
+            c->clock += kStepsPerHour;
+            c->cur ^= (int)(((int64_t)kStepsPerHour * c->P.n_sub) & 1);
+        } else {
+            st = step_dispatch(c, c->stream, 0, c->cur);
+            if (!st) st = tick(c, c->stream, 1);
+            c->clock += 1;
+            c->cur ^= (c->P.n_sub & 1);
+        }
+    }
+    if (!st) st = count_hour(c);
+    return st;
+}
+
+sim_status sim_fitness(sim_ctx* c, int32_t* out_count, double* out_fitness) {
+    if (!c) return SIM_EINVAL;
+    cudaError_t e = cudaMemsetAsync(c->ws + c->lay.final_count, 0, sizeof(int32_t) * c->n, c->stream);
+    if (e) return cuda_check(c, e, "fitness memset");
+    k_count<<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
+        c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock),
+        c->at<uint32_t>(c->lay.cell), c->at<int32_t>(c->lay.final_count), 1, 0);
+    if (sim_status st = cuda_check(c, cudaGetLastError(), "k_count launch")) return st;
+    std::vector<int32_t> cnt(c->n);
+    e = cudaMemcpyAsync(cnt.data(), c->ws + c->lay.final_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e) return cuda_check(c, e, "fitness copy");
+    if (sim_status st = read_status(c)) return st;
+    for (int p = 0; p < c->n; ++p) {
+        if (out_count) out_count[p] = cnt[p];
+        if (out_fitness) out_fitness[p] = c->cfg.n_max_fitness - (double)cnt[p];
+    }
+    return SIM_OK;
+}
+
+sim_status sim_counts(sim_ctx* c, int32_t* out, int hours) {
+    if (!c || !out) return SIM_EINVAL;
+    if (hours != c->cfg.hours) return fail(c, SIM_EINVAL, "hours must equal the configured count length");
+    const size_t n = (size_t)c->n * (hours + 1);
+    cudaError_t e =
+        cudaMemcpyAsync(out, c->ws + c->lay.counts, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e) return cuda_check(c, e, "counts copy");
+    if (sim_status st = read_status(c)) return st;
+    for (int p = 0; p < c->n; ++p) {
+        const int64_t last = c->proto[p].t_end < c->clock ? c->proto[p].t_end : c->clock;
+        for (int h = 0; h <= hours; ++h)
+            if ((int64_t)h * kStepsPerHour > last || h > c->counted_hour) out[(size_t)p * (hours + 1) + h] = -1;
+    }
+    return SIM_OK;
+}
+
+sim_status sim_delivered_dose(sim_ctx* c, double* out) {
+    if (!c || !out) return SIM_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(out, c->ws + c->lay.cum, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e) return cuda_check(c, e, "dose copy");
+    return read_status(c);
+}
+
+sim_status sim_clock(sim_ctx* c, int64_t* step, int64_t* t_end) {
+    if (!c) return SIM_EINVAL;
+    for (int p = 0; p < c->n; ++p) {
+        if (step) step[p] = c->clock < c->proto[p].t_end ? c->clock : c->proto[p].t_end;
+        if (t_end) t_end[p] = c->proto[p].t_end;
+    }
+    return SIM_OK;
+}
+
+sim_status sim_set_clock(sim_ctx* c, int64_t step) {
+    if (!c || step < 0 || step >= (int64_t)0xffffffffLL) return SIM_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.clock, &step, sizeof step, cudaMemcpyHostToDevice, c->stream);
+    // stale claims carry step tags that could outrank the new clock: clear them with the work-list counters
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.claim, 0, 8 * (size_t)c->total_sites, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.icount, 0, 8, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_check(c, e, "set clock");
+    c->clock = step;
+    c->counted_hour = step / kStepsPerHour - (step % kStepsPerHour == 0 ? 1 : 0);
+    return SIM_OK;
+}
+
+sim_status sim_get_state(sim_ctx* c, int p, float* O, float* G, float* H, uint32_t* cell) {
+    if (!c || p < 0 || p >= c->n) return SIM_EINVAL;
+    const Proto& pr = c->proto[p];
+    const int64_t n = (int64_t)pr.L * pr.L * pr.L;
+    const size_t es = elem_size(c->cfg.precision);
+    std::vector<char> tmp((size_t)(n * es));
+    float* dst[3] = {O, G, H};
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 3 && !e; ++f) {
+        if (!dst[f]) continue;
+        e = cudaMemcpyAsync(tmp.data(), (char*)c->field(c->cur, f) + pr.site0 * es, n * es, cudaMemcpyDeviceToHost,
+                            c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+        if (e) break;
+        if (c->cfg.precision == SIM_FP32) std::memcpy(dst[f], tmp.data(), n * 4);
+        else if (c->cfg.precision == SIM_BF16) to_float<__nv_bfloat16>(tmp.data(), dst[f], n);
+        else to_float<__half>(tmp.data(), dst[f], n);
+    }
+    if (!e && cell)
+        e = cudaMemcpyAsync(cell, c->at<uint32_t>(c->lay.cell) + pr.site0, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_check(c, e, "get state");
+    return read_status(c);
+}
+
+sim_status sim_set_state(sim_ctx* c, int p, const float* O, const float* G, const float* H, const uint32_t* cell) {
+    if (!c || p < 0 || p >= c->n) return SIM_EINVAL;
+    const Proto& pr = c->proto[p];
+    const int64_t n = (int64_t)pr.L * pr.L * pr.L;
+    const size_t es = elem_size(c->cfg.precision);
+    const float* src[3] = {O, G, H};
+    std::vector<char> tmp((size_t)(n * es));
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 3 && !e; ++f) {
+        if (!src[f]) continue;
+        if (c->cfg.precision == SIM_FP32) std::memcpy(tmp.data(), src[f], n * 4);
+        else if (c->cfg.precision == SIM_BF16)
+            for (int64_t i = 0; i < n; ++i) ((__nv_bfloat16*)tmp.data())[i] = __float2bfloat16_rn(src[f][i]);
+        else
+            for (int64_t i = 0; i < n; ++i) ((__half*)tmp.data())[i] = __float2half_rn(src[f][i]);
+        for (int b = 0; b < 2 && !e; ++b)  // both buffers: faces are read from either
+            e = cudaMemcpyAsync((char*)c->field(b, f) + pr.site0 * es, tmp.data(), n * es, cudaMemcpyHostToDevice,
+                                c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+    }
+    if (!e && cell)
+        e = cudaMemcpyAsync(c->at<uint32_t>(c->lay.cell) + pr.site0, cell, n * 4, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "set state");
+}
+
+sim_status sim_save_state(sim_ctx* c, void* buf, size_t* bytes) {
+    if (!c || !bytes) return SIM_EINVAL;
+    const size_t es = elem_size(c->cfg.precision);
+    const size_t ncnt = (size_t)c->n * (c->cfg.hours + 1);
+    const size_t need = ckpt_bytes(c);
+    if (!buf) {
+        *bytes = need;
+        return SIM_OK;
+    }
+    if (*bytes < need) return fail(c, SIM_ENOSPC, "checkpoint buffer too small");
+    CkptHeader h{};
+    std::memcpy(h.magic, "GPUGACK1", 8);
+    h.n = c->n;
+    h.precision = c->cfg.precision;
+    h.total_sites = c->total_sites;
+    h.clock = c->clock;
+    h.counted_hour = c->counted_hour;
+    h.cur = c->cur;
+    h.hours = c->cfg.hours;
+    char* out = (char*)buf;
+    std::memcpy(out, &h, sizeof h);
+    size_t off = sizeof h;
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 3 && !e; ++f, off += es * c->total_sites)
+        e = cudaMemcpyAsync(out + off, c->field(c->cur, f), es * c->total_sites, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(out + off, c->ws + c->lay.cell, 4 * c->total_sites, cudaMemcpyDeviceToHost, c->stream);
+    off += 4 * c->total_sites;
+    if (!e) e = cudaMemcpyAsync(out + off, c->ws + c->lay.cum, 8 * c->n, cudaMemcpyDeviceToHost, c->stream);
+    off += 8 * c->n;
+    if (!e) e = cudaMemcpyAsync(out + off, c->ws + c->lay.counts, 4 * ncnt, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_check(c, e, "save state");
+    *bytes = need;
+    return read_status(c);
+}
+
+sim_status sim_load_state(sim_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf || bytes < sizeof(CkptHeader)) return SIM_EINVAL;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    const size_t es = elem_size(c->cfg.precision);
+    const size_t ncnt = (size_t)c->n * (c->cfg.hours + 1);
+    if (std::memcmp(h.magic, "GPUGACK1", 8) || h.n != c->n || h.precision != c->cfg.precision ||
+        h.total_sites != c->total_sites || h.hours != c->cfg.hours || bytes < ckpt_bytes(c))
+        return fail(c, SIM_EINVAL, "checkpoint does not match this context");
+    const char* in = (const char*)buf;
+    size_t off = sizeof h;
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 3 && !e; ++f, off += es * c->total_sites)
+        for (int b = 0; b < 2 && !e; ++b)
+            e = cudaMemcpyAsync(c->field(b, f), in + off, es * c->total_sites, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->ws + c->lay.cell, in + off, 4 * c->total_sites, cudaMemcpyHostToDevice, c->stream);
+    off += 4 * c->total_sites;
+    if (!e) e = cudaMemcpyAsync(c->ws + c->lay.cum, in + off, 8 * c->n, cudaMemcpyHostToDevice, c->stream);
+    off += 8 * c->n;
+    if (!e) e = cudaMemcpyAsync(c->ws + c->lay.counts, in + off, 4 * ncnt, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->ws + c->lay.clock, &h.clock, sizeof h.clock, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.claim, 0, 8 * (size_t)c->total_sites, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.icount, 0, 8, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_check(c, e, "load state");
+    c->clock = h.clock;
+    c->counted_hour = h.counted_hour;
+    c->cur = 0;  // both buffers hold the restored state
+    return SIM_OK;
+}
+
+void sim_destroy(sim_ctx* c) {
+    if (!c) return;
+    drop_graphs(c);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    delete c;
+}
+
+}  // extern "C"

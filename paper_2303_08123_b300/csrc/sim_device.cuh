@@ -1,0 +1,126 @@
+// sim_device.cuh -- device-side types and helpers of libsim (sm_103a).
+//
+// Lattice state lives in HBM as structure-of-arrays over the whole batch: one
+// array per field (O2, glucose, H+), double-buffered, plus one 32-bit cell
+// word, one 64-bit division claim and the division work list.  Protocol p owns
+// sites [site0[p], site0[p] + L_p^3) of every array, index x + L (y + L z).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace simdev {
+
+// Cell word: bits 0..2 kind, bit 3 DOOMED, bits 4.. age (steps in the phase).
+constexpr uint32_t kEmpty = 0, kG1 = 1, kS = 2, kG2 = 3, kM = 4, kQ = 5;
+constexpr uint32_t kKindMask = 7u, kDoomed = 8u;
+constexpr int kAgeShift = 4;
+// Philox counter word 2 ("purpose") separates the streams of one site and step.
+constexpr uint32_t kPurposeInit = 0, kPurposeIrr = 1, kPurposeDiv = 2;
+// model switches
+constexpr int kFDivision = 1, kFDeath = 2, kFQuiescence = 4, kFReaction = 8, kFDiffusion = 16,
+              kFDoomImmediate = 32;
+
+constexpr int kStepsPerHour = 600;  // paper: 600 CA steps per simulated hour
+
+// FP32 model parameters as the kernels use them (pH thresholds already turned
+// into H+ concentrations in mM so no kernel takes a logarithm).
+struct Params {
+    int dur[4];
+    int n_sub;
+    int flags;
+    float lam[3];
+    float med[3];  // medium O2, glucose, H+ (mM)
+    float q_O, K_O, q_G, K_G, k_an, O_an, q_H, f_Q;
+    float alpha, beta, omf_m, omf_K;
+    float phi[5];
+    float O_q, G_q, H_q, G_d, H_d;
+    uint32_t key0, key1, init_word;
+};
+
+struct Proto {
+    int32_t L;
+    int32_t R;
+    int64_t site0;   // first site of this protocol in the batch arrays
+    int64_t t_end;   // horizon in steps; the protocol is frozen from then on
+    int32_t frac0;   // first entry in the fraction table
+    int32_t nfrac;   // fractions (distinct steps)
+};
+
+// Work list entry: `n` consecutive sites of protocol `p` starting at local
+// index `begin`.  Ragged batches are just lists of such entries.
+struct Block {
+    int32_t p;
+    int32_t n;
+    int64_t begin;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based, so every
+// (site, step, purpose, protocol) tuple has its own independent draw and a run
+// resumed from a checkpoint repeats itself exactly.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in [0,1) from the top 24 bits: exact in FP32
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
+// floor(u24(x) * n) in exact integer arithmetic
+__device__ __forceinline__ uint32_t pick24(uint32_t x, uint32_t n) {
+    return (uint32_t)(((uint64_t)(x >> 8) * (uint64_t)n) >> 24);
+}
+
+// ---------------------------------------------------------------------------
+// storage precision of the fields: FP32 compute, FP32 / BF16 / FP16 storage
+template <typename T>
+__device__ __forceinline__ float ld(const T* p);
+template <>
+__device__ __forceinline__ float ld<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <>
+__device__ __forceinline__ float ld<__half>(const __half* p) { return __half2float(*p); }
+
+template <typename T>
+__device__ __forceinline__ T cvt(float v);
+template <>
+__device__ __forceinline__ float cvt<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half cvt<__half>(float v) { return __float2half_rn(v); }
+
+__device__ __forceinline__ bool is_face(int L, int x, int y, int z) {
+    return x == 0 || y == 0 || z == 0 || x == L - 1 || y == L - 1 || z == L - 1;
+}
+
+// Dose delivered to protocol `pr` at `step` (fractions on one step were merged
+// on the host).  Fraction tables hold at most a few hundred entries.
+__device__ __forceinline__ double dose_at(const Proto& pr, const int64_t* __restrict__ fstep,
+                                          const double* __restrict__ fdose, int64_t step) {
+    for (int j = 0; j < pr.nfrac; ++j)
+        if (fstep[pr.frac0 + j] == step) return fdose[pr.frac0 + j];
+    return 0.0;
+}
+
+// Protocol owning global site g (site0 is ascending).
+__device__ __forceinline__ int owner(const Proto* __restrict__ protos, int n, int64_t g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (protos[mid].site0 <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace simdev

@@ -1,0 +1,213 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: fields within 1e-5 of the medium value per step (FP32 against FP64
+arithmetic), discrete cell state bit-exact except where the oracle flags a
+decision whose margin lies inside that tolerance (and the 2-hop neighbourhood
+such a decision can reach through division).
+"""
+import numpy as np
+import pytest
+
+from synth.params import P0, F_DEFAULT, F_DIVISION
+from tests import _parity as par
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x00C0_FFEE_0000_0042
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_08123_b300 import _build
+    _build.build()
+    return torch
+
+
+def _sim(L, R, **kw):
+    from paper_2303_08123_b300 import Simulator
+    kw.setdefault("seed", SEED)
+    return Simulator(L, R, **kw)
+
+
+def _load_single_fraction(sim, step, doses):
+    """Slot p receives doses[p] Gy at `step` (a multiple of 300) or nothing."""
+    from paper_2303_08123_b300 import csr
+    prot = [([d], [step / 600.0]) if d > 0 else ([], []) for d in doses]
+    sim.load_protocols(*csr(prot))
+
+
+# ----------------------------------------------------------------------------- init
+def test_seeded_spheroid_bit_exact(cuda, orc):
+    L = [8, 13, 40, 64, 33]
+    R = [2, 4, 5, 8, -1]
+    sim = _sim(L, R)
+    for p, (l, r) in enumerate(zip(L, R)):
+        O, G, H, cell = sim.get_state(p)
+        ref = orc.init(P0, l, r, SEED)
+        assert np.array_equal(cell, ref.cell), p
+        assert np.all(O == np.float32(P0.medium_O)) and np.all(G == np.float32(P0.medium_G))
+        assert np.allclose(H, ref.H, rtol=1e-7)
+    assert int(np.count_nonzero(sim.get_state(2)[3] & 7)) == 515
+    assert int(np.count_nonzero(sim.get_state(3)[3] & 7)) == 2109
+
+
+# ----------------------------------------------------------------------------- one step
+@pytest.mark.parametrize("case", ["plain", "dose", "doom_immediate", "no_quiescence"])
+def test_one_step_parity_ragged_batch(cuda, orc, case):
+    """A ragged batch (8^3, 13^3 with a ragged tail block, 24^3, 40^3) of crowded
+    random states; one step with and without a fraction."""
+    L = [8, 13, 24, 40]
+    p = P0
+    if case == "doom_immediate":
+        p = P0.replace(flags=F_DEFAULT | 32)
+    if case == "no_quiescence":
+        p = P0.replace(flags=F_DEFAULT & ~4)
+    doses = [0.0] * 4 if case == "plain" else [2.0, 5.0, 1.25, 3.0]
+    step = 300 * 7
+    sim = _sim(L, [-1] * 4, params=p)
+    _load_single_fraction(sim, step, doses)
+    states = []
+    for i, l in enumerate(L):
+        fields, cell = par.random_state(l, 100 + i)
+        sim.set_state(i, *fields, cell)
+        states.append((fields, cell))
+    sim.set_clock(step)
+    sim.run(1)
+    for i, l in enumerate(L):
+        st = par.oracle_state(orc, l, *states[i])
+        near, stats = orc.step(p, st, SEED, i, step, dose=doses[i])
+        O, G, H, gcell = sim.get_state(i)
+        r = par.compare(l, (O, G, H), gcell, st, near)
+        assert r["field_err"] <= par.FIELD_TOL, (l, r)
+        assert r["unexplained"] == 0, (l, r)
+        if doses[i] > 0:
+            assert stats["n_doomed_new"] + stats["n_deaths"] > 0
+    np.testing.assert_allclose(sim.delivered_dose(), doses)
+
+
+def test_one_step_parity_large_lattice(cuda, orc):
+    """64^3 (256 work-list blocks) crowded state, fraction at the step."""
+    L, step = 64, 600
+    sim = _sim([L], [-1])
+    _load_single_fraction(sim, step, [2.0])
+    fields, cell = par.random_state(L, 7)
+    sim.set_state(0, *fields, cell)
+    sim.set_clock(step)
+    sim.run(1)
+    st = par.oracle_state(orc, L, fields, cell)
+    near, stats = orc.step(P0, st, SEED, 0, step, dose=2.0)
+    g = sim.get_state(0)
+    r = par.compare(L, g[:3], g[3], st, near)
+    assert r["field_err"] <= par.FIELD_TOL and r["unexplained"] == 0, r
+    assert stats["n_divisions"] > 100
+
+
+# ----------------------------------------------------------------------------- runs
+def test_run_parity_counts_and_state(cuda, orc):
+    """1,500 steps from the seeded spheroid with a 3 Gy fraction at 30 min: hourly
+    counts equal, final cells bit-exact, fields within 1e-4 after the run."""
+    from paper_2303_08123_b300 import csr
+    L, R, T = 24, 5, 1500
+    doses, waits = [3.0], [0.5]
+    sim = _sim([L], [R], hours=2, t_end_steps=T)
+    sim.load_protocols(*csr([(doses, waits)]))
+    sim.run(0)
+    ref = orc.run(P0, L, R, SEED, 0, doses, waits, t_end_steps=T, hours=2)
+    O, G, H, cell = sim.get_state(0)
+    assert np.array_equal(cell, ref["state"].cell), ref["stats"]
+    assert np.array_equal(sim.counts()[0], ref["counts"])
+    for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
+        assert np.max(np.abs(g - o)) / m < 1e-4
+    n, f = sim.fitness()
+    assert n[0] == ref["stats"]["n_live"] and f[0] == 1500 - n[0]
+    assert sim.delivered_dose()[0] == 3.0
+
+
+def test_graph_replay_equals_plain_launches(cuda):
+    """The hour-graph path and per-step launches run the same kernels with the
+    same Philox counters: results are identical bit for bit."""
+    from paper_2303_08123_b300 import csr
+    L, R = [16, 24, 20], [3, 5, 4]
+    out = []
+    for graphs in (True, False):
+        sim = _sim(L, R, use_graphs=graphs, hours=3, t_end_steps=1800)
+        sim.load_protocols(*csr([([2.0, 1.0], [0.5, 1.0])] * 3))
+        sim.run(0)
+        out.append([sim.get_state(p) for p in range(3)] + [sim.counts()])
+        sim.close()
+    for a, b in zip(out[0][:3], out[1][:3]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(out[0][3], out[1][3])
+
+
+def test_checkpoint_resume_bit_exact(cuda):
+    from paper_2303_08123_b300 import csr
+    L, R = [16, 20], [4, 4]
+    prot = csr([([2.0, 2.0], [0.5, 1.0]), ([4.0], [1.5])])
+    a = _sim(L, R, hours=2, t_end_steps=1200)
+    a.load_protocols(*prot)
+    a.run(450)
+    blob = a.save_state()
+    a.run(0)
+    b = _sim(L, R, hours=2, t_end_steps=1200)
+    b.load_protocols(*prot)
+    b.load_state(blob)
+    b.run(0)
+    for p in range(2):
+        for x, y in zip(a.get_state(p), b.get_state(p)):
+            assert np.array_equal(x, y)
+    assert np.array_equal(a.counts(), b.counts())
+    np.testing.assert_array_equal(a.delivered_dose(), b.delivered_dose())
+
+
+def test_horizon_fitness_and_frozen_protocols(cuda):
+    from paper_2303_08123_b300 import csr
+    sim = _sim([12, 12], [3, 3], regrowth_h=1, hours=4)
+    sim.load_protocols(*csr([([1.0], [0.5]), ([1.0, 1.0], [0.5, 2.0])]))
+    _, t_end = sim.clock()
+    assert list(t_end) == [300 + 600, 1500 + 600]
+    sim.run(0)
+    step, _ = sim.clock()
+    assert list(step) == [900, 2100]
+    c = sim.counts()
+    assert c[0, 2] == -1 and c[0, 1] >= 0 and c[1, 3] >= 0 and c[1, 4] == -1
+    n, f = sim.fitness()
+    assert np.all(f == 1500 - n)
+    np.testing.assert_allclose(sim.delivered_dose(), [1.0, 2.0])
+
+
+def test_protocol_validation(cuda):
+    from paper_2303_08123_b300 import SimError, csr
+    sim = _sim([10], [2], dose_cap_gy=10.0)
+    for bad in ([([-1.0], [1.0])], [([1.0], [0.25])], [([6.0, 6.0], [1.0, 1.0])], [([1.0], [-0.5])]):
+        with pytest.raises(SimError) as e:
+            sim.load_protocols(*csr(bad))
+        assert e.value.status == -1
+    with pytest.raises(SimError):
+        sim.run(1)  # nothing loaded yet
+    sim.load_protocols(*csr([([10.0], [0.0])]))  # exactly at the cap, at t = 0
+    sim.run(1)
+    assert sim.delivered_dose()[0] == 10.0
+
+
+def test_division_claims_resolve_like_oracle_under_contention(cuda, orc):
+    """Many end-of-M cells around few free sites, division only."""
+    L = 16
+    p = P0.replace(flags=F_DIVISION)
+    sim = _sim([L], [-1], params=p)
+    _load_single_fraction(sim, 0, [0.0])
+    rng = np.random.default_rng(9)
+    inner = par.interior_mask(L)
+    durM = int(P0.dur_h[3] * 600)
+    cell = np.where(inner & (rng.random(L ** 3) < 0.8), 4 | (durM << 4), 0).astype(np.uint32)
+    f = [np.full(L ** 3, v, dtype=np.float32) for v in par.medium()]
+    sim.set_state(0, *f, cell)
+    sim.set_clock(12345)
+    sim.run(1)
+    st = par.oracle_state(orc, L, f, cell)
+    orc.step(p, st, SEED, 0, 12345)
+    assert np.array_equal(sim.get_state(0)[3], st.cell)
