@@ -1,0 +1,325 @@
+"""Throughput benchmark: GA protocols evaluated per second on one B300.
+
+Workload (per GPU): a GA population of 256 protocols on identical 64^3
+lattices, each starting from the same seeded spheroid of radius 8 (2,109
+cells); 10 fractions per protocol with doses from {0.5, ..., 2.5} Gy and waits
+from {6, ..., 60} h, total dose capped at 20 Gy; FP32 fields; horizon = last
+fraction + 120 h.  A bench step is one simulated hour (600 CA steps) of the
+whole batch, all hot-path kernels included (irradiation, reaction-diffusion,
+cell update, division, hourly counts).  protocols/s = protocol-steps per second
+divided by the batch's mean horizon in steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one batch per rank (weak scaling, no collective on
+the data path).  `--impl reference` times the FP64 CPU oracle on this host's
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import workloads  # noqa: E402
+from synth.params import P0  # noqa: E402
+
+N_PROT, L, R = 256, 64, 8
+SEED = 0x5EED_2023
+METRIC = "GA protocols evaluated/sec"
+UNIT = "protocols/s"
+STEPS_PER_HOUR = 600
+
+
+def workload():
+    prot = workloads.ga_batch(N_PROT, seed=2)
+    t_end_h = [sum(w) + 120.0 for _, w in prot]
+    return prot, float(np.mean(t_end_h))
+
+
+def workload_config(mean_t_end_h, precision="fp32"):
+    return {
+        "workload": f"ga_batch {N_PROT} protocols x {L}^3 lattice, seeded spheroid R={R} (2109 cells), "
+                    "10 fractions/protocol, doses {0.5..2.5} Gy, waits {6..60} h, cap 20 Gy, "
+                    f"{precision} fields, n_sub={P0.n_sub}",
+        "step": "one simulated hour (600 CA steps) of the whole batch",
+        "protocols_per_s": "protocol-steps/s divided by the mean horizon (last fraction + 120 h)",
+        "mean_horizon_h": round(mean_t_end_h, 2),
+        "l2": "working set > 126 MB L2 (fields alone 805 MB): no flush needed",
+        "parallelism": "independent protocol batch per GPU",
+    }
+
+
+# --------------------------------------------------------------------------- helpers
+def _csr(protocols):
+    off, d, w = [0], [], []
+    for dd, ww in protocols:
+        d.extend(dd)
+        w.extend(ww)
+        off.append(len(d))
+    return np.array(off, dtype=np.int32), np.array(d, dtype=np.float64), np.array(w, dtype=np.float64)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2303_08123_b300", "csrc", d["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["dram_bytes_per_launch"] if sha == d["source_sha"] else None
+
+
+def cpu_baseline(mean_t_end_h, max_steps=None):
+    """The FP64 oracle on this host's cores: one protocol per core, a bounded
+    number of steps each; extrapolated to whole protocols by the mean horizon."""
+    import oracle
+    cores = os.cpu_count() or 1
+    prot, _ = workload()
+    n = min(cores, N_PROT)
+    steps = max_steps or 120
+    off, d, w = _csr(prot[:n])
+    t0 = time.perf_counter()
+    res = oracle.run_batch(P0, [L] * n, [R] * n, SEED, off, d, w, max_steps=steps, n_threads=n)
+    dt = time.perf_counter() - t0
+    site_steps = float(np.sum(res["steps"])) * L ** 3
+    per_protocol = mean_t_end_h * STEPS_PER_HOUR * L ** 3
+    return {"value": site_steps / dt / per_protocol, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} protocols x {steps} steps of the {L}^3 workload on {n} threads "
+                      f"({dt:.1f} s); extrapolated by the {mean_t_end_h:.1f} h mean horizon",
+            "site_steps_per_s": site_steps / dt}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prot, mean_h = workload()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(mean_h, max_steps=20)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(mean_h, max_steps=40))
+    v = statistics.mean(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(mean_h), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2303_08123_b300 import Simulator, csr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prot, mean_h = workload()
+    off, d, w = csr(prot)
+    K, W = args.steps, args.warmup
+    hours = W + K + 2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim = Simulator([L] * N_PROT, [R] * N_PROT, seed=SEED, precision=args.precision, hours=hours,
+                    dose_cap_gy=20.0, device=dev)
+    sim.load_protocols(off, d, w)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(W):
+        sim.run(STEPS_PER_HOUR)
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(K):
+            sim.run(STEPS_PER_HOUR)
+        stop.record(stream)
+        barrier()
+    ms = start.elapsed_time(stop)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    ms_per_step = ms / K
+    sites = N_PROT * L ** 3
+    protocol_steps_per_s = world * N_PROT * STEPS_PER_HOUR * K / (ms / 1e3)
+    value = protocol_steps_per_s / (mean_h * STEPS_PER_HOUR)
+    site_steps_per_s = protocol_steps_per_s * L ** 3
+    launches_per_step = STEPS_PER_HOUR * (P0.n_sub + 3) + 2  # substeps, cell, claim, resolve; tick, count
+
+    # per-kernel device time over plain steps of the same batch (CUDA events on the launching stream)
+    kms, kl = sim.profile_steps(60)
+    interior = (L - 2) ** 3 * N_PROT
+    es = 4 if args.precision == "fp32" else 2
+    alg_bytes = interior * (6 * es + 4)  # read 3 fields + cell word, write 3 fields
+    sub_ms = kms[0] / kl[0]
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / (sub_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_substep", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
+            "traffic": traffic_for("k_substep"),
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sub_ms,
+            "kernel_share": {k: float(v / kms.sum()) for k, v in zip(("substep", "cell", "claim", "resolve"), kms)}}
+    step_bytes = 32 if args.precision == "fp32" else 20
+    roof_step = {"fused_alg_bytes_per_site_step": step_bytes,
+                 "achieved_GBps": site_steps_per_s / world * step_bytes / 1e9,
+                 "frac": site_steps_per_s / world * step_bytes / 1e9 / hbm}
+
+    # end to end through the public API with host buffers: protocol table H2D
+    # (and spheroid reseed) inside the timed region, fitness read back every step
+    barrier()
+    t0 = time.perf_counter()
+    sim.load_protocols(off, d, w)
+    for _ in range(K):
+        sim.run(STEPS_PER_HOUR)
+        cnt, fit = sim.fitness()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * N_PROT * STEPS_PER_HOUR * K / e2e_s / (mean_h * STEPS_PER_HOUR)
+    h2d = (off.nbytes + d.nbytes + w.nbytes) / K
+    d2h = cnt.nbytes + fit.nbytes
+
+    # plain form: one protocol at a time, per-step launches, no graph
+    plain = Simulator([L], [R], seed=SEED, precision=args.precision, use_graphs=False, dose_cap_gy=20.0,
+                      device=dev)
+    po, pd, pw = csr(prot[:1])
+    plain.load_protocols(po, pd, pw)
+    plain.run(50)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plain.run(STEPS_PER_HOUR)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_val = STEPS_PER_HOUR / (a.elapsed_time(b) / 1e3) / (mean_h * STEPS_PER_HOUR)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
+                "config": workload_config(mean_h, args.precision),
+                "site_updates_per_s": site_steps_per_s,
+                "roofline": roof, "step_roofline": roof_step,
+                "plain": {"value": plain_val, "unit": UNIT,
+                          "how": "one protocol per launch sequence, per-step launches, no graph"},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches_per_step * K,
+                "clocks": clk.summary()}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(mean_h)
+        print(json.dumps(line))
+    sim.close()
+    plain.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--protocols", type=int, default=256, help="batch size per GPU (smaller: profiling cases)")
+    args = ap.parse_args()
+    global N_PROT
+    N_PROT = args.protocols
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -149,6 +149,16 @@ sim_status sim_set_state(sim_ctx* ctx, int p, const float* O, const float* G, co
 sim_status sim_save_state(sim_ctx* ctx, void* buf, size_t* bytes);
 sim_status sim_load_state(sim_ctx* ctx, const void* buf, size_t bytes);
 
+/*
+ * Advance every protocol by n_steps steps with plain launches (no graph) and
+ * time each kernel class with CUDA events on the context's stream.  ms (4
+ * entries) receives the summed device time in milliseconds of: [0] the n_sub
+ * reaction-diffusion substeps, [1] the cell update, [2] the division claims,
+ * [3] the division resolution; launches (4 entries, may be NULL) the number
+ * of kernel launches of each class.  Same results as sim_run.  Synchronises.
+ */
+sim_status sim_profile_steps(sim_ctx* ctx, int n_steps, double* ms, int64_t* launches);
+
 /* Message of the last failed call on this context ("" if none). */
 const char* sim_last_error(const sim_ctx* ctx);
 const char* sim_status_string(sim_status s);

@@ -169,13 +169,14 @@ sim_status reset_device(sim_ctx* c) {
 
 // One CA step for every protocol, reading the step index as clock + k_off.
 template <typename T>
-sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf) {
+sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, cudaEvent_t* ev = nullptr) {
     const unsigned nb = (unsigned)c->blocks.size();
     const Block* blocks = c->at<Block>(c->lay.blocks);
     const Proto* protos = c->at<Proto>(c->lay.proto);
     const int64_t* clock = c->at<int64_t>(c->lay.clock);
     uint32_t* cell = c->at<uint32_t>(c->lay.cell);
     int buf = start_buf;
+    if (ev) cudaEventRecord(ev[0], s);
     for (int sub = 0; sub < c->P.n_sub; ++sub) {
         k_substep<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, sub == 0, (const T*)c->field(buf, 0),
                                              (const T*)c->field(buf, 1), (const T*)c->field(buf, 2),
@@ -184,25 +185,29 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf) {
                                              c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum), c->P);
         buf ^= 1;
     }
+    if (ev) cudaEventRecord(ev[1], s);
     k_cell<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, (const T*)c->field(buf, 0),
                                       (const T*)c->field(buf, 1), (const T*)c->field(buf, 2), cell,
                                       c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->P);
     // the work list is short (cells at the end of M): a fixed grid strides over it
     const unsigned ng = 148 * 4;
+    if (ev) cudaEventRecord(ev[2], s);
     k_claim<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                     c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
                                     c->at<unsigned long long>(c->lay.claim), c->P);
+    if (ev) cudaEventRecord(ev[3], s);
     k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                       c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
                                       c->at<unsigned long long>(c->lay.claim));
+    if (ev) cudaEventRecord(ev[4], s);
     return cuda_check(c, cudaGetLastError(), "step launch");
 }
 
-sim_status step_dispatch(sim_ctx* c, cudaStream_t s, int k_off, int start_buf) {
+sim_status step_dispatch(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, cudaEvent_t* ev = nullptr) {
     switch (c->cfg.precision) {
-        case SIM_BF16: return enqueue_step<__nv_bfloat16>(c, s, k_off, start_buf);
-        case SIM_FP16: return enqueue_step<__half>(c, s, k_off, start_buf);
-        default: return enqueue_step<float>(c, s, k_off, start_buf);
+        case SIM_BF16: return enqueue_step<__nv_bfloat16>(c, s, k_off, start_buf, ev);
+        case SIM_FP16: return enqueue_step<__half>(c, s, k_off, start_buf, ev);
+        default: return enqueue_step<float>(c, s, k_off, start_buf, ev);
     }
 }
 
@@ -473,6 +478,47 @@ sim_status sim_run(sim_ctx* c, int64_t max_steps) {
     return st;
 }
 
+sim_status sim_profile_steps(sim_ctx* c, int n_steps, double* ms, int64_t* launches) {
+    if (!c || !ms || n_steps < 0) return SIM_EINVAL;
+    if (!c->loaded) return fail(c, SIM_ESTATE, "load protocols before running");
+    for (int k = 0; k < 4; ++k) {
+        ms[k] = 0.0;
+        if (launches) launches[k] = 0;
+    }
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k)
+        if (cudaError_t e = cudaEventCreate(&ev[k])) return cuda_check(c, e, "event create");
+    sim_status st = SIM_OK;
+    for (int i = 0; i < n_steps && st == SIM_OK; ++i) {
+        st = count_hour(c);
+        if (!st) st = step_dispatch(c, c->stream, 0, c->cur, ev);
+        if (!st) st = tick(c, c->stream, 1);
+        if (st) break;
+        c->clock += 1;
+        c->cur ^= (c->P.n_sub & 1);
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e) {
+            st = cuda_check(c, e, "event sync");
+            break;
+        }
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            ms[k] += t;
+        }
+        if (launches) {
+            launches[0] += c->P.n_sub;
+            launches[1] += 1;
+            launches[2] += 1;
+            launches[3] += 1;
+        }
+    }
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    if (!st) st = count_hour(c);
+    if (!st) st = read_status(c);
+    return st;
+}
+
 sim_status sim_fitness(sim_ctx* c, int32_t* out_count, double* out_fitness) {
     if (!c) return SIM_EINVAL;
     cudaError_t e = cudaMemsetAsync(c->ws + c->lay.final_count, 0, sizeof(int32_t) * c->n, c->stream);
@@ -569,6 +615,16 @@ sim_status sim_set_state(sim_ctx* c, int p, const float* O, const float* G, cons
     const int64_t n = (int64_t)pr.L * pr.L * pr.L;
     const size_t es = elem_size(c->cfg.precision);
     const float* src[3] = {O, G, H};
+    if (cell) {  // cells only on interior sites and with a valid kind
+        const int L = pr.L;
+        for (int64_t s = 0; s < n; ++s) {
+            const uint32_t k = cell[s] & kKindMask;
+            if (k == kEmpty) continue;
+            const int x = (int)(s % L), y = (int)((s / L) % L), z = (int)(s / ((int64_t)L * L));
+            if (k > kQ || x == 0 || y == 0 || z == 0 || x == L - 1 || y == L - 1 || z == L - 1)
+                return fail(c, SIM_EINVAL, "cell word at site " + std::to_string(s) + " is invalid or on a face");
+        }
+    }
     std::vector<char> tmp((size_t)(n * es));
     cudaError_t e = cudaSuccess;
     for (int f = 0; f < 3 && !e; ++f) {

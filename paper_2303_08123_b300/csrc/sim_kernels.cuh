@@ -222,6 +222,10 @@ __global__ void __launch_bounds__(kThreads) k_claim(const Proto* __restrict__ pr
         const int L = pr.L;
         const int64_t s = g - pr.site0;
         const int x = (int)(s % L), y = (int)((s / L) % L), z = (int)(s / ((int64_t)L * L));
+        if (is_face(L, x, y, z)) {  // cells never sit on faces; never read past the lattice
+            target[i] = 0xffffffffu;
+            continue;
+        }
         uint32_t freebits = 0;  // bit j: j-th Moore neighbour in lexicographic order is free
         int j = 0;
 #pragma unroll

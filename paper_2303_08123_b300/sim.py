@@ -86,6 +86,7 @@ SIGNATURES = {
     "sim_set_state": (ctypes.c_int, [_vp, ctypes.c_int, _f32p, _f32p, _f32p, _u32p]),
     "sim_save_state": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
     "sim_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "sim_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _i64p]),
     "sim_last_error": (ctypes.c_char_p, [_vp]),
     "sim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sim_destroy": (None, [_vp]),
@@ -236,6 +237,14 @@ class Simulator:
         f = [np.ascontiguousarray(a, dtype=np.float32) for a in (O, G, H)]
         c = np.ascontiguousarray(cell, dtype=np.uint32)
         self._call("sim_set_state", p, *(_ptr(a, ctypes.c_float) for a in f), _ptr(c, ctypes.c_uint32))
+
+    def profile_steps(self, n_steps: int):
+        """Advance n_steps plain steps; per-kernel-class device ms and launch counts
+        (substep, cell, claim, resolve)."""
+        ms = np.zeros(4, dtype=np.float64)
+        nl = np.zeros(4, dtype=np.int64)
+        self._call("sim_profile_steps", int(n_steps), _ptr(ms, ctypes.c_double), _ptr(nl, ctypes.c_int64))
+        return ms, nl
 
     def save_state(self) -> bytes:
         size = ctypes.c_size_t(0)
