@@ -150,7 +150,7 @@ def cpu_baseline(mean_t_end_h, max_steps=None):
     cores = os.cpu_count() or 1
     prot, _ = workload()
     n = min(cores, N_PROT)
-    steps = max_steps or 120
+    steps = max_steps or 1200
     off, d, w = _csr(prot[:n])
     t0 = time.perf_counter()
     res = oracle.run_batch(P0, [L] * n, [R] * n, SEED, off, d, w, max_steps=steps, n_threads=n)
