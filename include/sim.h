@@ -159,6 +159,36 @@ sim_status sim_load_state(sim_ctx* ctx, const void* buf, size_t bytes);
  */
 sim_status sim_profile_steps(sim_ctx* ctx, int n_steps, double* ms, int64_t* launches);
 
+/*
+ * Allocation-free reaction-diffusion step for one FP32 lattice (no
+ * counterpart in the paper; this is a service for callers that cannot
+ * allocate device memory).  Some hosts hand every byte of device memory to
+ * their own pool allocator and forbid stray cudaMalloc calls, and some
+ * latency-bound loops cannot afford the device-wide synchronisation a
+ * cudaMalloc/cudaFree may cause; such callers cannot provide the workspace
+ * sim_create needs.  This entry point needs none: it runs the n_sub
+ * substeps of one CA step (with the dose fraction of that step applied to
+ * the cell words first, exactly as sim_run does for protocol slot 0) on the
+ * caller's device arrays O, G, H (mM, L^3 floats each) and cell (L^3 words),
+ * in place, on `cuda_stream` (NULL = legacy default stream).  The ping-pong
+ * field buffer and the small launch tables live in one fixed device array
+ * inside the library, 3 MiB + 64 KiB, that every GPU which loads the library
+ * keeps until the process exits.
+ *  - Sizes: 8 <= L <= 64.  A larger lattice is rejected with SIM_ENOSPC
+ *    before any work is enqueued; cfg->precision must be SIM_FP32.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins.
+ *  - All calls share the one array and each call overwrites it (it keeps the
+ *    last call's contents): calls that overlap on the GPU, e.g. on two
+ *    streams, race and corrupt each other's results.  Serialise them.
+ *  - No device memory is allocated or freed; the call is asynchronous.
+ * Errors: SIM_EINVAL (NULL pointer, bad config, negative dose or step),
+ * SIM_ENOSPC (L > 64), SIM_ECUDA.
+ */
+sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, double dose_gy, float* O, float* G,
+                               float* H, uint32_t* cell, void* cuda_stream);
+
 /* Message of the last failed call on this context ("" if none). */
 const char* sim_last_error(const sim_ctx* ctx);
 const char* sim_status_string(sim_status s);

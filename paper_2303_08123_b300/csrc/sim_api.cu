@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -720,3 +721,102 @@ void sim_destroy(sim_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free reaction-diffusion step (sim_diffuse_noalloc).  For callers
+// that cannot allocate device memory: the ping-pong field buffer and the
+// launch tables live in this fixed file-scope device array, which every GPU
+// that loads the library holds until the process exits.  Host code must not
+// use the array's name as a device address (on the host it is only a
+// stand-in); the real address comes from cudaGetSymbolAddress, looked up once
+// per device.
+namespace {
+constexpr int kNoallocMaxL = 64;
+constexpr size_t kNoallocMaxSites = (size_t)kNoallocMaxL * kNoallocMaxL * kNoallocMaxL;
+constexpr size_t kNoallocFieldBytes = 3 * sizeof(float) * kNoallocMaxSites;  // 3 MiB
+constexpr size_t kNoallocTableBytes = 64 * 1024;
+constexpr int kNoallocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocFieldBytes + kNoallocTableBytes];
+
+namespace {
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_base[kNoallocMaxDevices] = {};
+
+// byte offsets of the launch tables behind the field buffer
+constexpr size_t kNaProto = kNoallocFieldBytes;
+constexpr size_t kNaBlocks = kNaProto + 256;
+constexpr size_t kNaMaxBlocks = (kNoallocMaxSites + kSitesPerBlock - 1) / kSitesPerBlock;
+constexpr size_t kNaFstep = kNaBlocks + sizeof(Block) * kNaMaxBlocks;
+constexpr size_t kNaFdose = kNaFstep + 64;
+constexpr size_t kNaClock = kNaFdose + 64;
+constexpr size_t kNaCum = kNaClock + 64;
+static_assert(kNaCum + 64 <= kNoallocFieldBytes + kNoallocTableBytes, "no-alloc tables overflow the scratch array");
+}  // namespace
+
+extern "C" sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, double dose_gy, float* O,
+                                          float* G, float* H, uint32_t* cell, void* cuda_stream) {
+    if (!cfg || !O || !G || !H || !cell) return SIM_EINVAL;
+    std::string why;
+    if (!valid_config(cfg, &why) || cfg->precision != SIM_FP32) return SIM_EINVAL;
+    if (L < 8) return SIM_EINVAL;
+    if (L > kNoallocMaxL) return SIM_ENOSPC;  // the fixed scratch holds at most 64^3 sites
+    if (step < 0 || step >= (int64_t)0xffffffffLL || !(dose_gy >= 0.0) || !std::isfinite(dose_gy)) return SIM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return SIM_ECUDA;
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_base[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SIM_ECUDA;
+            g_noalloc_base[dev] = (unsigned char*)p;
+        }
+        base = g_noalloc_base[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const Params P = make_params(*cfg);
+    const int64_t sites = (int64_t)L * L * L;
+    Proto pr{};
+    pr.L = L;
+    pr.R = -1;
+    pr.site0 = 0;
+    pr.t_end = step + 1;
+    pr.frac0 = 0;
+    pr.nfrac = dose_gy > 0.0 ? 1 : 0;
+    std::vector<Block> blocks;
+    for (int64_t b = 0; b < sites; b += kSitesPerBlock) {
+        Block bl{};
+        bl.p = 0;
+        bl.begin = b;
+        bl.n = (int)((sites - b) < kSitesPerBlock ? (sites - b) : kSitesPerBlock);
+        blocks.push_back(bl);
+    }
+    const double zero = 0.0;
+    // host-to-device copies from pageable memory return once the source has been staged
+    cudaError_t e = cudaMemcpyAsync(base + kNaProto, &pr, sizeof pr, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + kNaBlocks, blocks.data(), sizeof(Block) * blocks.size(), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + kNaFstep, &step, sizeof step, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + kNaFdose, &dose_gy, sizeof dose_gy, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + kNaClock, &step, sizeof step, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + kNaCum, &zero, sizeof zero, cudaMemcpyHostToDevice, s);
+    // the scratch buffer starts as a copy of the caller's fields so both buffers hold the same Dirichlet faces
+    float* buf[2][3] = {{O, G, H},
+                        {(float*)base, (float*)base + kNoallocMaxSites, (float*)base + 2 * kNoallocMaxSites}};
+    for (int f = 0; f < 3 && !e; ++f)
+        e = cudaMemcpyAsync(buf[1][f], buf[0][f], sizeof(float) * sites, cudaMemcpyDeviceToDevice, s);
+    if (e) return SIM_ECUDA;
+    int cur = 0;
+    for (int sub = 0; sub < P.n_sub; ++sub) {
+        k_substep<float><<<(unsigned)blocks.size(), kThreads, 0, s>>>(
+            (const Block*)(base + kNaBlocks), (const Proto*)(base + kNaProto), (const int64_t*)(base + kNaClock), 0,
+            sub == 0, buf[cur][0], buf[cur][1], buf[cur][2], buf[cur ^ 1][0], buf[cur ^ 1][1], buf[cur ^ 1][2], cell,
+            (const int64_t*)(base + kNaFstep), (const double*)(base + kNaFdose), (double*)(base + kNaCum), P);
+        cur ^= 1;
+    }
+    for (int f = 0; f < 3 && cur == 1 && !e; ++f)  // odd n_sub: the result sits in the scratch buffer
+        e = cudaMemcpyAsync(buf[0][f], buf[1][f], sizeof(float) * sites, cudaMemcpyDeviceToDevice, s);
+    if (e || cudaGetLastError() != cudaSuccess) return SIM_ECUDA;
+    return SIM_OK;
+}

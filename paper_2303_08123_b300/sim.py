@@ -87,6 +87,8 @@ SIGNATURES = {
     "sim_save_state": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
     "sim_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "sim_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _i64p]),
+    "sim_diffuse_noalloc": (ctypes.c_int, [_P(SimConfig), ctypes.c_int, ctypes.c_int64, ctypes.c_double, _vp, _vp,
+                                           _vp, _vp, _vp]),
     "sim_last_error": (ctypes.c_char_p, [_vp]),
     "sim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sim_destroy": (None, [_vp]),
