@@ -56,7 +56,7 @@ def workload_config(mean_t_end_h, precision="fp32"):
         "step": "one simulated hour (600 CA steps) of the whole batch",
         "protocols_per_s": "protocol-steps/s divided by the mean horizon (last fraction + 120 h)",
         "mean_horizon_h": round(mean_t_end_h, 2),
-        "l2": "working set > 126 MB L2 (fields alone 805 MB): no flush needed",
+        "l2": "working set > 126 MB L2 (fields alone 805 MB at 256 protocols): no flush needed",
         "parallelism": "independent protocol batch per GPU",
     }
 
@@ -129,9 +129,10 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+def traffic_for(kernel, n_protocols):
+    """DRAM bytes per launch from the committed ncu summary (per 64^3 protocol,
+    scaled to the batch), or None when the kernel source changed since the
+    counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -140,7 +141,7 @@ def traffic_for(kernel):
         return None
     src = os.path.join(ROOT, "paper_2303_08123_b300", "csrc", d["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return d["dram_bytes_per_launch"] if sha == d["source_sha"] else None
+    return d["dram_bytes_per_protocol"] * n_protocols if sha == d["source_sha"] else None
 
 
 def cpu_baseline(mean_t_end_h, max_steps=None):
@@ -211,8 +212,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sim = Simulator([L] * N_PROT, [R] * N_PROT, seed=SEED, precision=args.precision, hours=hours,
-                    dose_cap_gy=20.0, device=dev)
+                    dose_cap_gy=20.0, device=dev, path=args.path)
     sim.load_protocols(off, d, w)
+    shape, shape_ms = sim.autotune(10) if args.path == "fused" else (0, None)  # re-seeds the batch at step 0
     stream = torch.cuda.current_stream(dev)
     for _ in range(W):
         sim.run(STEPS_PER_HOUR)
@@ -234,21 +236,34 @@ def run_ours(args):
     protocol_steps_per_s = world * N_PROT * STEPS_PER_HOUR * K / (ms / 1e3)
     value = protocol_steps_per_s / (mean_h * STEPS_PER_HOUR)
     site_steps_per_s = protocol_steps_per_s * L ** 3
-    launches_per_step = STEPS_PER_HOUR * (P0.n_sub + 3) + 2  # substeps, cell, claim, resolve; tick, count
+    per_ca_step = ((P0.n_sub + 1) // 2 + 2) if args.path == "fused" else (P0.n_sub + 3)
+    launches_per_step = STEPS_PER_HOUR * per_ca_step + 2  # passes (or substeps + cell), claim, resolve; tick, count
 
     # per-kernel device time over plain steps of the same batch (CUDA events on the launching stream)
     kms, kl = sim.profile_steps(60)
     interior = (L - 2) ** 3 * N_PROT
     es = 4 if args.precision == "fp32" else 2
-    alg_bytes = interior * (6 * es + 4)  # read 3 fields + cell word, write 3 fields
-    sub_ms = kms[0] / kl[0]
+    if args.path == "fused":
+        kn = "k_fused1" if shape in (3, 4) else "k_fused"
+        classes = {f"{kn} (first pass: irradiation + 2 substeps)": (kms[0], kl[0], interior * (6 * es + 4)),
+                   f"{kn} (last pass: 2 substeps + cell update)": (kms[1], kl[1], interior * (6 * es + 8))}
+        traffic_key = {f"{kn} (first pass: irradiation + 2 substeps)": f"{kn}_first_shape{shape}",
+                       f"{kn} (last pass: 2 substeps + cell update)": f"{kn}_last_shape{shape}"}
+    else:
+        classes = {"k_substep": (kms[0], kl[0], interior * (6 * es + 4)),
+                   "k_cell": (kms[1], kl[1], interior * (3 * es + 8))}
+        traffic_key = {"k_substep": "k_substep", "k_cell": "k_cell"}
+    name = max(classes, key=lambda k: classes[k][0])
+    k_ms, k_n, alg_bytes = classes[name]
+    avg_ms = k_ms / k_n
     hbm, peak_kind = peaks()
-    achieved = alg_bytes / (sub_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_substep", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
-            "traffic": traffic_for("k_substep"),
-            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sub_ms,
-            "kernel_share": {k: float(v / kms.sum()) for k, v in zip(("substep", "cell", "claim", "resolve"), kms)}}
+            "traffic": traffic_for(traffic_key[name], N_PROT),
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+            "kernel_share": {k: float(v / kms.sum()) for k, v in
+                             zip(("reaction-diffusion", "cell-update pass", "claim", "resolve"), kms)}}
     step_bytes = 32 if args.precision == "fp32" else 20
     roof_step = {"fused_alg_bytes_per_site_step": step_bytes,
                  "achieved_GBps": site_steps_per_s / world * step_bytes / 1e9,
@@ -286,7 +301,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
-                "config": workload_config(mean_h, args.precision),
+                "config": dict(workload_config(mean_h, args.precision), path=args.path, tile_shape=shape,
+                               autotune_ms_per_step=None if shape_ms is None else [round(x, 4) for x in shape_ms]),
                 "site_updates_per_s": site_steps_per_s,
                 "roofline": roof, "step_roofline": roof_step,
                 "plain": {"value": plain_val, "unit": UNIT,
@@ -312,6 +328,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", default="fused", choices=["fused", "substep"])
     ap.add_argument("--protocols", type=int, default=256, help="batch size per GPU (smaller: profiling cases)")
     args = ap.parse_args()
     global N_PROT

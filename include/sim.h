@@ -71,15 +71,29 @@ typedef struct {
     int32_t max_fractions;  /* capacity of each protocol's fraction table */
     uint32_t init_word;     /* Philox protocol word of the seeded spheroid */
     int32_t use_graphs;     /* 1: replay each simulated hour as one CUDA graph */
+    int32_t path;           /* SIM_PATH_FUSED (default) or SIM_PATH_SUBSTEP */
+    int32_t tile_shape;     /* fused tile: 0 auto; 1 = 32 x 16, 2 = 16 x 16 with two columns per
+                               thread (packed FP32); 3 = 32 x 16, 4 = 16 x 16 with one column per
+                               thread (FP32 storage only) */
+    int32_t z_chunk;        /* fused z range per CTA: 0 auto, else planes per CTA */
 } sim_config;
+
+/* Kernel paths (same results, bit for bit, with FP32 storage):
+ *  SIM_PATH_FUSED    temporally blocked passes of two substeps each, the last one
+ *                    fused with the cell update (each site read and written once
+ *                    per pass);
+ *  SIM_PATH_SUBSTEP  one kernel per substep plus a separate cell-update kernel.
+ * With BF16/FP16 storage the fused path needs even lattice sides and an even
+ * n_sub; other contexts run the substep path. */
+enum { SIM_PATH_FUSED = 0, SIM_PATH_SUBSTEP = 1 };
 
 typedef struct sim_ctx sim_ctx;
 
 /*
  * Device workspace needed for n protocols on lattices L[0..n-1] (each 8..1024).
- * Fields are stored double-buffered in the configured precision; per site the
- * workspace holds 2 x 3 field values, a 4-byte cell word, an 8-byte division
- * claim and 8 bytes of division work list.  Errors: SIM_EINVAL on NULL or
+ * Fields and cell words are stored double-buffered (fields in the configured
+ * precision); per site the workspace holds 2 x 3 field values, 2 x 4-byte cell
+ * words, an 8-byte division claim and 8 bytes of division work list.  Errors: SIM_EINVAL on NULL or
  * out-of-range arguments.
  */
 sim_status sim_workspace_size(const sim_config* cfg, int n, const int32_t* L, size_t* bytes);
@@ -152,10 +166,13 @@ sim_status sim_load_state(sim_ctx* ctx, const void* buf, size_t bytes);
 /*
  * Advance every protocol by n_steps steps with plain launches (no graph) and
  * time each kernel class with CUDA events on the context's stream.  ms (4
- * entries) receives the summed device time in milliseconds of: [0] the n_sub
- * reaction-diffusion substeps, [1] the cell update, [2] the division claims,
- * [3] the division resolution; launches (4 entries, may be NULL) the number
- * of kernel launches of each class.  Same results as sim_run.  Synchronises.
+ * entries) receives the summed device time in milliseconds of: [0] the
+ * reaction-diffusion work before the cell update (fused path: every pass but
+ * the last; substep path: the n_sub substep kernels), [1] the cell update
+ * (fused path: the last pass, which also runs its substeps; substep path: the
+ * cell-update kernel), [2] the division claims, [3] the division resolution;
+ * launches (4 entries, may be NULL) the number of kernel launches of each
+ * class.  Same results as sim_run.  Synchronises.
  */
 sim_status sim_profile_steps(sim_ctx* ctx, int n_steps, double* ms, int64_t* launches);
 
@@ -188,6 +205,16 @@ sim_status sim_profile_steps(sim_ctx* ctx, int n_steps, double* ms, int64_t* lau
  */
 sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, double dose_gy, float* O, float* G,
                                float* H, uint32_t* cell, void* cuda_stream);
+
+/*
+ * Autotuner of the fused path: time n_steps plain steps of this context's own
+ * batch with every applicable tile shape (sim_config.tile_shape 1..4), keep the
+ * fastest, then re-seed every spheroid and set the clock to 0 (call it right
+ * after sim_load_protocols).  *best (may be NULL) receives the chosen shape
+ * (0 on the substep path); ms (4 entries, may be NULL) the device milliseconds
+ * per step of each shape, -1 where a shape does not apply.  Synchronises.
+ */
+sim_status sim_autotune(sim_ctx* ctx, int n_steps, int* best, double* ms);
 
 /* Message of the last failed call on this context ("" if none). */
 const char* sim_last_error(const sim_ctx* ctx);

@@ -8,11 +8,13 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
 #include "../../include/sim.h"
 #include "sim_kernels.cuh"
+#include "sim_fused.cuh"
 
 using namespace simdev;
 
@@ -28,11 +30,11 @@ size_t elem_size(int precision) { return precision == SIM_FP32 ? 4 : 2; }
 
 // Byte offsets of every region of the workspace.
 struct Layout {
-    size_t proto, blocks, fstep, fdose, field[2][3], cell, claim, intents, target, icount, counts, cum, clock,
-        status, final_count, total;
+    size_t proto, blocks, tiles, fstep, fdose, field[2][3], cell[2], claim, intents, target, icount, counts, cum,
+        clock, status, final_count, total;
 };
 
-Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks) {
+Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks, int64_t ntiles) {
     Layout l{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -44,11 +46,13 @@ Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nb
     const int64_t nf = (int64_t)n * cfg.max_fractions;
     l.proto = take(sizeof(Proto) * n);
     l.blocks = take(sizeof(Block) * nblocks);
+    l.tiles = take(sizeof(Tile) * (ntiles > 0 ? ntiles : 1));
     l.fstep = take(sizeof(int64_t) * (nf > 0 ? nf : 1));
     l.fdose = take(sizeof(double) * (nf > 0 ? nf : 1));
     for (int b = 0; b < 2; ++b)
         for (int f = 0; f < 3; ++f) l.field[b][f] = take(es * total_sites);
-    l.cell = take(4 * total_sites);
+    l.cell[0] = take(4 * total_sites);
+    l.cell[1] = take(4 * total_sites);
     l.claim = take(8 * total_sites);
     l.intents = take(4 * total_sites);
     l.target = take(4 * total_sites);
@@ -76,7 +80,64 @@ bool valid_config(const sim_config* cfg, std::string* why) {
     if (cfg->hours < 0 || cfg->hours > 1000000) return *why = "hours out of range", false;
     if (cfg->max_fractions < 0 || cfg->max_fractions > 100000) return *why = "max_fractions out of range", false;
     if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
+    if (cfg->path < SIM_PATH_FUSED || cfg->path > SIM_PATH_SUBSTEP) return *why = "unknown kernel path", false;
+    if (cfg->tile_shape < 0 || cfg->tile_shape > 4) return *why = "tile_shape must be in 0..4", false;
+    if (cfg->tile_shape > 2 && cfg->precision != SIM_FP32) return *why = "column-per-thread shapes need FP32", false;
+    if (cfg->z_chunk < 0) return *why = "z_chunk must be >= 0", false;
     return true;
+}
+
+// Tile shapes of the fused kernels: (x extent, y extent); shapes 1-2 run two
+// columns per thread (packed f32x2), shapes 3-4 one column per thread.
+constexpr int kNumShapes = 4;
+constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0}, {32, 16}, {16, 16}, {32, 16}, {16, 16}};
+constexpr int kTargetCtas = 2 * 148;  // at least two CTAs per SM when the batch allows it
+
+// Tile shape: the one covering the fewest sites (ties: the larger tile).
+int pick_shape(const sim_config& cfg, int n, const int32_t* L) {
+    if (cfg.tile_shape) return cfg.tile_shape;
+    int64_t best = -1;
+    int pick = 1;
+    for (int sh = 1; sh <= 2; ++sh) {  // default: packed shapes; the autotuner may pick any
+        int64_t area = 0;
+        for (int p = 0; p < n; ++p) {
+            const int64_t tx = (L[p] + kTileShapes[sh][0] - 1) / kTileShapes[sh][0];
+            const int64_t ty = (L[p] + kTileShapes[sh][1] - 1) / kTileShapes[sh][1];
+            area += tx * kTileShapes[sh][0] * ty * kTileShapes[sh][1] * (int64_t)L[p];
+        }
+        if (best < 0 || area < best) best = area, pick = sh;
+    }
+    return pick;
+}
+
+// Fused work list: column tiles of every protocol, split in z when the batch
+// has too few columns to fill the GPU.
+std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int shape) {
+    const int TX = kTileShapes[shape][0], TY = kTileShapes[shape][1];
+    int64_t cols = 0;
+    for (int p = 0; p < n; ++p) cols += (int64_t)((L[p] + TX - 1) / TX) * ((L[p] + TY - 1) / TY);
+    std::vector<Tile> t;
+    for (int p = 0; p < n; ++p) {
+        int zc = L[p];
+        if (cfg.z_chunk > 0) zc = cfg.z_chunk;
+        else if (cols < kTargetCtas) {
+            const int64_t nz = (kTargetCtas + cols - 1) / cols;
+            zc = (int)((L[p] + nz - 1) / nz);
+            if (zc < 8) zc = 8;
+        }
+        for (int z = 0; z < L[p]; z += zc)
+            for (int y = 0; y < L[p]; y += TY)
+                for (int x = 0; x < L[p]; x += TX) {
+                    Tile e{};
+                    e.p = p;
+                    e.x0 = (int16_t)x;
+                    e.y0 = (int16_t)y;
+                    e.z0 = (int16_t)z;
+                    e.z1 = (int16_t)((z + zc) < L[p] ? z + zc : L[p]);
+                    t.push_back(e);
+                }
+    }
+    return t;
 }
 
 }  // namespace
@@ -87,6 +148,9 @@ struct sim_ctx {
     int n = 0;
     std::vector<Proto> proto;
     std::vector<Block> blocks;
+    std::vector<Tile> tiles;
+    int shape = 1;
+    int vec_ok = 1;  // every lattice side even: column pairs start on even elements
     int64_t total_sites = 0;
     Layout lay{};
     char* ws = nullptr;
@@ -94,14 +158,22 @@ struct sim_ctx {
     cudaStream_t capture_stream = nullptr;
     int64_t clock = 0;          // host mirror of the device clock
     int cur = 0;                // field buffer holding the current state
+    int ccur = 0;               // cell-word buffer holding the current state
     int64_t counted_hour = -1;  // last hour whose counts were recorded
     bool loaded = false;
-    cudaGraphExec_t hour_graph[2] = {nullptr, nullptr};  // indexed by the starting buffer
+    cudaGraphExec_t hour_graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by (field, cell) start buffers
     std::string err;
 
     template <typename T>
     T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
     void* field(int buf, int f) const { return ws + lay.field[buf][f]; }
+    uint32_t* cells(int buf) const { return reinterpret_cast<uint32_t*>(ws + lay.cell[buf]); }
+    bool fused() const { return cfg.path == SIM_PATH_FUSED; }
+    // substeps per fused pass: passes of two, one pass of one for an odd remainder
+    int passes() const { return (P.n_sub + 1) / 2; }
+    int pass_k(int j) const { return (j == passes() - 1 && (P.n_sub & 1)) ? 1 : 2; }
+    int field_flips() const { return fused() ? passes() : P.n_sub; }
+    int cell_flips() const { return fused() ? 1 : 0; }
 };
 
 namespace {
@@ -143,7 +215,7 @@ template <typename T>
 sim_status launch_init(sim_ctx* c) {
     k_init<T><<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
         c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), (T*)c->field(0, 0), (T*)c->field(0, 1),
-        (T*)c->field(0, 2), (T*)c->field(1, 0), (T*)c->field(1, 1), (T*)c->field(1, 2), c->at<uint32_t>(c->lay.cell),
+        (T*)c->field(0, 2), (T*)c->field(1, 0), (T*)c->field(1, 1), (T*)c->field(1, 2), c->cells(0),
         c->at<unsigned long long>(c->lay.claim), c->P);
     return cuda_check(c, cudaGetLastError(), "k_init launch");
 }
@@ -164,18 +236,136 @@ sim_status reset_device(sim_ctx* c) {
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.status, 0, sizeof(uint32_t), c->stream);
     c->clock = 0;
     c->cur = 0;
+    c->ccur = 0;
     c->counted_hour = -1;
     return cuda_check(c, e, "reset");
 }
 
 // One CA step for every protocol, reading the step index as clock + k_off.
+template <typename T, int TX, int TY, int K, bool EPI>
+void launch_fused_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout) {
+    using Sh = FusedShape<TX, TY, K>;
+    k_fused<T, TX, TY, K, EPI><<<(unsigned)c->tiles.size(), Sh::THREADS, fused_smem_bytes<T, TX, TY, K>(), s>>>(
+        c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first,
+        (c->vec_ok && K % 2 == 0) ? 1 : 0, (const T*)c->field(buf, 0), (const T*)c->field(buf, 1), (const T*)c->field(buf, 2), (T*)c->field(buf ^ 1, 0),
+        (T*)c->field(buf ^ 1, 1), (T*)c->field(buf ^ 1, 2), cin, cout, c->at<int64_t>(c->lay.fstep),
+        c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum), c->at<uint32_t>(c->lay.intents),
+        c->at<uint32_t>(c->lay.icount), c->P);
+}
+
+template <int TX, int TY, int K, bool EPI>
+void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin,
+                     uint32_t* cout) {
+    using Sh = FusedShape1<TX, TY, K>;
+    k_fused1<TX, TY, K, EPI><<<(unsigned)c->tiles.size(), Sh::THREADS, fused1_smem_bytes<TX, TY, K>(), s>>>(
+        c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first,
+        (const float*)c->field(buf, 0), (const float*)c->field(buf, 1), (const float*)c->field(buf, 2),
+        (float*)c->field(buf ^ 1, 0), (float*)c->field(buf ^ 1, 1), (float*)c->field(buf ^ 1, 2), cin, cout,
+        c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
+        c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->P);
+}
+
+template <typename T, int K, bool EPI>
+void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (c->shape == 3) return launch_fused1_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
+        if (c->shape == 4) return launch_fused1_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
+    }
+    if (c->shape == 2) launch_fused_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
+    else launch_fused_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
+}
+
+// allow the dynamic shared memory of every fused instantiation of type T (done once, outside any capture)
+template <typename T, int TX, int TY>
+cudaError_t fused_attrs_shape() {
+    cudaError_t e = cudaFuncSetAttribute(k_fused<T, TX, TY, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_smem_bytes<T, TX, TY, 1>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_fused<T, TX, TY, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_smem_bytes<T, TX, TY, 1>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_fused<T, TX, TY, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_smem_bytes<T, TX, TY, 2>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_fused<T, TX, TY, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_smem_bytes<T, TX, TY, 2>());
+    return e;
+}
+
+template <int TX, int TY>
+cudaError_t fused1_attrs_shape() {
+    cudaError_t e = cudaFuncSetAttribute(k_fused1<TX, TY, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused1_smem_bytes<TX, TY, 1>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_fused1<TX, TY, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused1_smem_bytes<TX, TY, 1>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_fused1<TX, TY, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused1_smem_bytes<TX, TY, 2>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_fused1<TX, TY, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused1_smem_bytes<TX, TY, 2>());
+    return e;
+}
+
 template <typename T>
-sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, cudaEvent_t* ev = nullptr) {
+cudaError_t fused_attrs() {
+    cudaError_t e = fused_attrs_shape<T, 32, 16>();
+    if (!e) e = fused_attrs_shape<T, 16, 16>();
+    if constexpr (std::is_same<T, float>::value) {
+        if (!e) e = fused1_attrs_shape<32, 16>();
+        if (!e) e = fused1_attrs_shape<16, 16>();
+    }
+    return e;
+}
+
+template <typename T>
+void launch_fused(sim_ctx* c, cudaStream_t s, int k_off, int K, bool epi, int first, int buf, const uint32_t* cin,
+                  uint32_t* cout) {
+    if (K == 1) {
+        if (epi) launch_fused_k<T, 1, true>(c, s, k_off, first, buf, cin, cout);
+        else launch_fused_k<T, 1, false>(c, s, k_off, first, buf, cin, cout);
+    } else {
+        if (epi) launch_fused_k<T, 2, true>(c, s, k_off, first, buf, cin, cout);
+        else launch_fused_k<T, 2, false>(c, s, k_off, first, buf, cin, cout);
+    }
+}
+
+// Events (profiling): ev[0] start, ev[1] after the reaction-diffusion work
+// without the cell update, ev[2] after the cell update (last fused pass or
+// k_cell), ev[3] after the claims, ev[4] after the resolution.
+template <typename T>
+sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, int start_cell,
+                        cudaEvent_t* ev = nullptr) {
     const unsigned nb = (unsigned)c->blocks.size();
     const Block* blocks = c->at<Block>(c->lay.blocks);
     const Proto* protos = c->at<Proto>(c->lay.proto);
     const int64_t* clock = c->at<int64_t>(c->lay.clock);
-    uint32_t* cell = c->at<uint32_t>(c->lay.cell);
+    const unsigned ng = 148 * 4;  // the division work list is short: a fixed grid strides over it
+    if (c->fused()) {
+        int buf = start_buf;
+        const int np = c->passes();
+        if (ev) cudaEventRecord(ev[0], s);
+        for (int j = 0; j < np; ++j) {
+            const bool epi = j == np - 1;
+            if (epi && ev) cudaEventRecord(ev[1], s);
+            uint32_t* cout = epi ? c->cells(start_cell ^ 1) : c->cells(start_cell);
+            launch_fused<T>(c, s, k_off, c->pass_k(j), epi, j == 0, buf, c->cells(start_cell), cout);
+            buf ^= 1;
+        }
+        if (ev) cudaEventRecord(ev[2], s);
+        uint32_t* cell = c->cells(start_cell ^ 1);
+        k_claim<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
+                                        c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
+                                        c->at<unsigned long long>(c->lay.claim), c->P);
+        if (ev) cudaEventRecord(ev[3], s);
+        k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
+                                          c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
+                                          c->at<unsigned long long>(c->lay.claim));
+        if (ev) cudaEventRecord(ev[4], s);
+        return cuda_check(c, cudaGetLastError(), "step launch");
+    }
+    uint32_t* cell = c->cells(start_cell);
     int buf = start_buf;
     if (ev) cudaEventRecord(ev[0], s);
     for (int sub = 0; sub < c->P.n_sub; ++sub) {
@@ -190,8 +380,6 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, cu
     k_cell<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, (const T*)c->field(buf, 0),
                                       (const T*)c->field(buf, 1), (const T*)c->field(buf, 2), cell,
                                       c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->P);
-    // the work list is short (cells at the end of M): a fixed grid strides over it
-    const unsigned ng = 148 * 4;
     if (ev) cudaEventRecord(ev[2], s);
     k_claim<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                     c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
@@ -204,12 +392,20 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, cu
     return cuda_check(c, cudaGetLastError(), "step launch");
 }
 
-sim_status step_dispatch(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, cudaEvent_t* ev = nullptr) {
+sim_status step_dispatch(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, int start_cell,
+                         cudaEvent_t* ev = nullptr) {
     switch (c->cfg.precision) {
-        case SIM_BF16: return enqueue_step<__nv_bfloat16>(c, s, k_off, start_buf, ev);
-        case SIM_FP16: return enqueue_step<__half>(c, s, k_off, start_buf, ev);
-        default: return enqueue_step<float>(c, s, k_off, start_buf, ev);
+        case SIM_BF16: return enqueue_step<__nv_bfloat16>(c, s, k_off, start_buf, start_cell, ev);
+        case SIM_FP16: return enqueue_step<__half>(c, s, k_off, start_buf, start_cell, ev);
+        default: return enqueue_step<float>(c, s, k_off, start_buf, start_cell, ev);
     }
+}
+
+// advance the host mirror of the buffer parities by `steps` steps
+void advance(sim_ctx* c, int64_t steps) {
+    c->clock += steps;
+    c->cur ^= (int)((steps * c->field_flips()) & 1);
+    c->ccur ^= (int)((steps * c->cell_flips()) & 1);
 }
 
 sim_status tick(sim_ctx* c, cudaStream_t s, int64_t by) {
@@ -222,7 +418,7 @@ sim_status count_hour(sim_ctx* c) {
     if (c->clock % kStepsPerHour != 0 || h > c->cfg.hours || h <= c->counted_hour) return SIM_OK;
     k_count<<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
         c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock),
-        c->at<uint32_t>(c->lay.cell), c->at<int32_t>(c->lay.counts), c->cfg.hours + 1, 1);
+        c->cells(c->ccur), c->at<int32_t>(c->lay.counts), c->cfg.hours + 1, 1);
     c->counted_hour = h;
     return cuda_check(c, cudaGetLastError(), "k_count launch");
 }
@@ -230,19 +426,21 @@ sim_status count_hour(sim_ctx* c) {
 // Capture one simulated hour (600 steps + clock advance) starting from field
 // buffer `start` as a CUDA graph.  Captured on a private stream; replayed on
 // the context's stream.
-sim_status build_hour_graph(sim_ctx* c, int start) {
-    if (c->hour_graph[start]) return SIM_OK;
+sim_status build_hour_graph(sim_ctx* c, int start, int cstart) {
+    const int key = start * 2 + cstart;
+    if (c->hour_graph[key]) return SIM_OK;
     cudaError_t e = cudaSuccess;
     if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
     if (e) return cuda_check(c, e, "capture stream");
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e) return cuda_check(c, e, "begin capture");
-    int buf = start;
+    int buf = start, cb = cstart;
     sim_status st = SIM_OK;
     for (int k = 0; k < kStepsPerHour && st == SIM_OK; ++k) {
-        st = step_dispatch(c, c->capture_stream, k, buf);
-        buf ^= (c->P.n_sub & 1);
+        st = step_dispatch(c, c->capture_stream, k, buf, cb);
+        buf ^= (c->field_flips() & 1);
+        cb ^= (c->cell_flips() & 1);
     }
     if (st == SIM_OK) st = tick(c, c->capture_stream, kStepsPerHour);
     e = cudaStreamEndCapture(c->capture_stream, &g);
@@ -251,7 +449,7 @@ sim_status build_hour_graph(sim_ctx* c, int start) {
         return st;
     }
     if (e) return cuda_check(c, e, "end capture");
-    e = cudaGraphInstantiate(&c->hour_graph[start], g, 0);
+    e = cudaGraphInstantiate(&c->hour_graph[key], g, 0);
     cudaGraphDestroy(g);
     return cuda_check(c, e, "graph instantiate");
 }
@@ -323,12 +521,18 @@ sim_status sim_workspace_size(const sim_config* cfg, int n, const int32_t* L, si
     int64_t total = 0, nb = 0;
     for (int p = 0; p < n; ++p) {
         if (L[p] < 8 || L[p] > kMaxL) return SIM_EINVAL;
+        if (cfg->z_chunk > 0 && cfg->z_chunk > L[p]) return SIM_EINVAL;
         const int64_t sites = (int64_t)L[p] * L[p] * L[p];
         total += sites;
         nb += (sites + kSitesPerBlock - 1) / kSitesPerBlock;
     }
     if (total >= (int64_t)0xffffffffLL) return SIM_EINVAL;  // work list holds 32-bit site indices
-    *bytes = make_layout(*cfg, n, total, nb).total;
+    int64_t nt = 0;  // room for the work list of any shape the autotuner may pick
+    for (int sh = 1; sh <= kNumShapes; ++sh) {
+        const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
+        nt = t > nt ? t : nt;
+    }
+    *bytes = make_layout(*cfg, n, total, nb, nt).total;
     return SIM_OK;
 }
 
@@ -368,9 +572,34 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
         c->proto.push_back(pr);
     }
     c->total_sites = site0;
-    c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size());
+    c->shape = pick_shape(*cfg, n, L);
+    for (int p = 0; p < n; ++p)
+        if (L[p] % 2) c->vec_ok = 0;
+    // 2-byte storage is staged in shared memory as aligned element pairs, which needs even lattice sides and
+    // passes of two substeps: other cases take the substep path
+    if (c->cfg.path == SIM_PATH_FUSED && c->cfg.precision != SIM_FP32 && (!c->vec_ok || (c->P.n_sub & 1)))
+        c->cfg.path = SIM_PATH_SUBSTEP;
+    if (c->cfg.path == SIM_PATH_FUSED) {
+        cudaError_t ea = c->cfg.precision == SIM_BF16   ? fused_attrs<__nv_bfloat16>()
+                         : c->cfg.precision == SIM_FP16 ? fused_attrs<__half>()
+                                                        : fused_attrs<float>();
+        if (ea) {
+            delete c;
+            return SIM_ECUDA;
+        }
+    }
+    c->tiles = make_tiles(*cfg, n, L, c->shape);
+    int64_t nt = 0;
+    for (int sh = 1; sh <= kNumShapes; ++sh) {
+        const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
+        nt = t > nt ? t : nt;
+    }
+    c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size(), nt);
     cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.blocks, c->blocks.data(), sizeof(Block) * c->blocks.size(),
                                     cudaMemcpyHostToDevice, c->stream);
+    if (!e)
+        e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
+                            cudaMemcpyHostToDevice, c->stream);
     if (!e)
         e = cudaMemcpyAsync(c->ws + c->lay.proto, c->proto.data(), sizeof(Proto) * n, cudaMemcpyHostToDevice,
                             c->stream);
@@ -462,17 +691,15 @@ sim_status sim_run(sim_ctx* c, int64_t max_steps) {
         st = count_hour(c);
         if (st) break;
         if (graphs && c->clock % kStepsPerHour == 0 && c->clock + kStepsPerHour <= target) {
-            st = build_hour_graph(c, c->cur);
+            st = build_hour_graph(c, c->cur, c->ccur);
             if (st) break;
-            cudaError_t e = cudaGraphLaunch(c->hour_graph[c->cur], c->stream);
+            cudaError_t e = cudaGraphLaunch(c->hour_graph[c->cur * 2 + c->ccur], c->stream);
             if (e) return cuda_check(c, e, "graph launch");
-            c->clock += kStepsPerHour;
-            c->cur ^= (int)(((int64_t)kStepsPerHour * c->P.n_sub) & 1);
+            advance(c, kStepsPerHour);
         } else {
-            st = step_dispatch(c, c->stream, 0, c->cur);
+            st = step_dispatch(c, c->stream, 0, c->cur, c->ccur);
             if (!st) st = tick(c, c->stream, 1);
-            c->clock += 1;
-            c->cur ^= (c->P.n_sub & 1);
+            advance(c, 1);
         }
     }
     if (!st) st = count_hour(c);
@@ -492,11 +719,10 @@ sim_status sim_profile_steps(sim_ctx* c, int n_steps, double* ms, int64_t* launc
     sim_status st = SIM_OK;
     for (int i = 0; i < n_steps && st == SIM_OK; ++i) {
         st = count_hour(c);
-        if (!st) st = step_dispatch(c, c->stream, 0, c->cur, ev);
+        if (!st) st = step_dispatch(c, c->stream, 0, c->cur, c->ccur, ev);
         if (!st) st = tick(c, c->stream, 1);
         if (st) break;
-        c->clock += 1;
-        c->cur ^= (c->P.n_sub & 1);
+        advance(c, 1);
         cudaError_t e = cudaEventSynchronize(ev[4]);
         if (e) {
             st = cuda_check(c, e, "event sync");
@@ -508,7 +734,7 @@ sim_status sim_profile_steps(sim_ctx* c, int n_steps, double* ms, int64_t* launc
             ms[k] += t;
         }
         if (launches) {
-            launches[0] += c->P.n_sub;
+            launches[0] += c->fused() ? c->passes() - 1 : c->P.n_sub;
             launches[1] += 1;
             launches[2] += 1;
             launches[3] += 1;
@@ -520,13 +746,72 @@ sim_status sim_profile_steps(sim_ctx* c, int n_steps, double* ms, int64_t* launc
     return st;
 }
 
+// Switch the fused work list to tile shape `sh` (rebuilds and uploads the tiles; drops captured graphs).
+sim_status set_shape(sim_ctx* c, int sh, const std::vector<int32_t>& L) {
+    c->shape = sh;
+    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh);
+    drop_graphs(c);
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "set shape");
+}
+
+sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
+    if (!c || n_steps < 1) return SIM_EINVAL;
+    if (!c->loaded) return fail(c, SIM_ESTATE, "load protocols before autotuning");
+    for (int k = 0; k < kNumShapes; ++k)
+        if (ms) ms[k] = -1.0;
+    if (!c->fused()) {
+        if (best) *best = 0;
+        return reset_device(c);
+    }
+    std::vector<int32_t> L(c->n);
+    for (int p = 0; p < c->n; ++p) L[p] = c->proto[p].L;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) || cudaEventCreate(&b)) return fail(c, SIM_ECUDA, "event create");
+    double best_ms = -1.0;
+    int pick = c->shape;
+    sim_status st = SIM_OK;
+    for (int sh = 1; sh <= kNumShapes && st == SIM_OK; ++sh) {
+        if (sh > 2 && c->cfg.precision != SIM_FP32) continue;
+        st = set_shape(c, sh, L);
+        // one untimed step (first touch), then n_steps timed plain steps
+        for (int i = 0; i <= n_steps && st == SIM_OK; ++i) {
+            if (i == 1) cudaEventRecord(a, c->stream);
+            st = step_dispatch(c, c->stream, 0, c->cur, c->ccur);
+            if (!st) st = tick(c, c->stream, 1);
+            advance(c, 1);
+        }
+        if (st) break;
+        cudaEventRecord(b, c->stream);
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e) {
+            st = cuda_check(c, e, "autotune sync");
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        if (ms) ms[sh - 1] = t / n_steps;
+        if (best_ms < 0 || t < best_ms) best_ms = t, pick = sh;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    st = set_shape(c, pick, L);
+    if (best) *best = pick;
+    if (!st) st = reset_device(c);  // the timing steps advanced the batch: start it again from step 0
+    if (!st) st = read_status(c);
+    return st;
+}
+
 sim_status sim_fitness(sim_ctx* c, int32_t* out_count, double* out_fitness) {
     if (!c) return SIM_EINVAL;
     cudaError_t e = cudaMemsetAsync(c->ws + c->lay.final_count, 0, sizeof(int32_t) * c->n, c->stream);
     if (e) return cuda_check(c, e, "fitness memset");
     k_count<<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
         c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock),
-        c->at<uint32_t>(c->lay.cell), c->at<int32_t>(c->lay.final_count), 1, 0);
+        c->cells(c->ccur), c->at<int32_t>(c->lay.final_count), 1, 0);
     if (sim_status st = cuda_check(c, cudaGetLastError(), "k_count launch")) return st;
     std::vector<int32_t> cnt(c->n);
     e = cudaMemcpyAsync(cnt.data(), c->ws + c->lay.final_count, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost,
@@ -604,7 +889,7 @@ sim_status sim_get_state(sim_ctx* c, int p, float* O, float* G, float* H, uint32
         else to_float<__half>(tmp.data(), dst[f], n);
     }
     if (!e && cell)
-        e = cudaMemcpyAsync(cell, c->at<uint32_t>(c->lay.cell) + pr.site0, n * 4, cudaMemcpyDeviceToHost, c->stream);
+        e = cudaMemcpyAsync(cell, c->cells(c->ccur) + pr.site0, n * 4, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_check(c, e, "get state");
     return read_status(c);
@@ -641,7 +926,7 @@ sim_status sim_set_state(sim_ctx* c, int p, const float* O, const float* G, cons
         if (!e) e = cudaStreamSynchronize(c->stream);
     }
     if (!e && cell)
-        e = cudaMemcpyAsync(c->at<uint32_t>(c->lay.cell) + pr.site0, cell, n * 4, cudaMemcpyHostToDevice, c->stream);
+        e = cudaMemcpyAsync(c->cells(c->ccur) + pr.site0, cell, n * 4, cudaMemcpyHostToDevice, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     return cuda_check(c, e, "set state");
 }
@@ -671,7 +956,7 @@ sim_status sim_save_state(sim_ctx* c, void* buf, size_t* bytes) {
     cudaError_t e = cudaSuccess;
     for (int f = 0; f < 3 && !e; ++f, off += es * c->total_sites)
         e = cudaMemcpyAsync(out + off, c->field(c->cur, f), es * c->total_sites, cudaMemcpyDeviceToHost, c->stream);
-    if (!e) e = cudaMemcpyAsync(out + off, c->ws + c->lay.cell, 4 * c->total_sites, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(out + off, c->cells(c->ccur), 4 * c->total_sites, cudaMemcpyDeviceToHost, c->stream);
     off += 4 * c->total_sites;
     if (!e) e = cudaMemcpyAsync(out + off, c->ws + c->lay.cum, 8 * c->n, cudaMemcpyDeviceToHost, c->stream);
     off += 8 * c->n;
@@ -697,7 +982,7 @@ sim_status sim_load_state(sim_ctx* c, const void* buf, size_t bytes) {
     for (int f = 0; f < 3 && !e; ++f, off += es * c->total_sites)
         for (int b = 0; b < 2 && !e; ++b)
             e = cudaMemcpyAsync(c->field(b, f), in + off, es * c->total_sites, cudaMemcpyHostToDevice, c->stream);
-    if (!e) e = cudaMemcpyAsync(c->ws + c->lay.cell, in + off, 4 * c->total_sites, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->cells(0), in + off, 4 * c->total_sites, cudaMemcpyHostToDevice, c->stream);
     off += 4 * c->total_sites;
     if (!e) e = cudaMemcpyAsync(c->ws + c->lay.cum, in + off, 8 * c->n, cudaMemcpyHostToDevice, c->stream);
     off += 8 * c->n;
@@ -709,7 +994,8 @@ sim_status sim_load_state(sim_ctx* c, const void* buf, size_t bytes) {
     if (e) return cuda_check(c, e, "load state");
     c->clock = h.clock;
     c->counted_hour = h.counted_hour;
-    c->cur = 0;  // both buffers hold the restored state
+    c->cur = 0;  // both field buffers hold the restored state
+    c->ccur = 0;
     return SIM_OK;
 }
 

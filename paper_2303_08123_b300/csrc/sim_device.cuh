@@ -123,4 +123,76 @@ __device__ __forceinline__ int owner(const Proto* __restrict__ protos, int n, in
     return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Arithmetic of one explicit substep, written with explicit round-to-nearest
+// intrinsics so that every kernel (scalar or packed f32x2) performs the same
+// operations in the same order and gets bit-identical FP32 results:
+//   s = ((((xm + xp) + ym) + yp) + zm) + zp;  lap = fma(-6, c, s);  t = fma(lam, lap, c)
+__device__ __forceinline__ float stencil_t(float c, float xm, float xp, float ym, float yp, float zm, float zp,
+                                           float lam) {
+    float s = __fadd_rn(xm, xp);
+    s = __fadd_rn(s, ym);
+    s = __fadd_rn(s, yp);
+    s = __fadd_rn(s, zm);
+    s = __fadd_rn(s, zp);
+    const float lap = __fmaf_rn(-6.f, c, s);
+    return __fmaf_rn(lam, lap, c);
+}
+
+// Uptake of one substep by a cell of the given kind:
+//   U_O = f q_O O/(O+K_O);  g = f q_G G/(G+K_G);  w = O_an/(O+O_an)
+//   U_G = g (1 + (k_an-1) w);  H+ release = q_H g k_an w
+// with f = 1 for cycling and f_Q for quiescent cells.
+__device__ __forceinline__ void uptake(uint32_t kind, float O, float Gv, const Params& P, float& uO, float& uG,
+                                       float& pH) {
+    const float f = (kind == kQ) ? P.f_Q : 1.f;
+    uO = __fdiv_rn(__fmul_rn(__fmul_rn(f, P.q_O), O), __fadd_rn(O, P.K_O));
+    const float gg = __fdiv_rn(__fmul_rn(__fmul_rn(f, P.q_G), Gv), __fadd_rn(Gv, P.K_G));
+    const float wa = __fdiv_rn(P.O_an, __fadd_rn(O, P.O_an));
+    uG = __fmul_rn(gg, __fmaf_rn(__fsub_rn(P.k_an, 1.f), wa, 1.f));
+    pH = __fmul_rn(__fmul_rn(__fmul_rn(P.q_H, gg), P.k_an), wa);
+}
+
+// Cell update of one site from its step-start word and post-diffusion fields:
+// necrosis if G < G_d or H > H_d; a G1 cell turns quiescent when O < O_q,
+// G < G_q or H > H_q and a quiescent cell returns to G1 once all three are
+// restored; cycling cells age and move on at the end of each phase; a cell
+// completing M dies if DOOMED, else it stays at the end of M (age capped) and
+// sets `want` (division intent).
+__device__ __forceinline__ uint32_t update_cell(uint32_t w, float O, float Gv, float H, const Params& P, bool& want) {
+    uint32_t kind = w & kKindMask;
+    if (kind == kEmpty) return w;
+    const uint32_t doomed = w & kDoomed;
+    uint32_t age = w >> kAgeShift;
+    if ((P.flags & kFDeath) && (Gv < P.G_d || H > P.H_d)) return kEmpty;
+    if (kind == kQ) {
+        if ((P.flags & kFQuiescence) && O >= P.O_q && Gv >= P.G_q && H <= P.H_q) return kG1 | doomed;
+        return w;
+    }
+    if (kind == kG1 && (P.flags & kFQuiescence) && (O < P.O_q || Gv < P.G_q || H > P.H_q)) return kQ | doomed;
+    age += 1;
+    if (age >= (uint32_t)P.dur[kind - 1]) {
+        if (kind < kM) {
+            kind += 1;
+            age = 0;
+        } else if (doomed) {
+            return kEmpty;  // mitotic catastrophe
+        } else {
+            age = (uint32_t)P.dur[kM - 1];
+            want = (P.flags & kFDivision) != 0;
+        }
+    }
+    return kind | doomed | (age << kAgeShift);
+}
+
+// LQ survival of a cell of the given kind at O2 level O under dose D:
+// S = exp(-a D - b D^2), a = alpha phi OMF(O), b = beta (phi OMF)^2,
+// OMF(O) = (m O + K)/(m (O + K)).
+__device__ __forceinline__ float lq_survival(uint32_t kind, float O, float dose, const Params& P) {
+    const float omf = (P.omf_m * O + P.omf_K) / (P.omf_m * (O + P.omf_K));
+    const float mod = P.phi[kind - 1] * omf;
+    const float a = P.alpha * mod, bq = P.beta * mod * mod;
+    return expf(-a * dose - bq * dose * dose);
+}
+
 }  // namespace simdev

@@ -93,10 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
         uint32_t w = cell[g];
         const uint32_t kind = w & kKindMask;
         if (dose > 0.f && kind != kEmpty) {
-            const float omf = (P.omf_m * O + P.omf_K) / (P.omf_m * (O + P.omf_K));
-            const float mod = P.phi[kind - 1] * omf;
-            const float a = P.alpha * mod, bq = P.beta * mod * mod;
-            const float S = expf(-a * dose - bq * dose * dose);
+            const float S = lq_survival(kind, O, dose, P);
             const uint4 r = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)step, kPurposeIrr, (uint32_t)b.p),
                                           P.key0, P.key1);
             if (u24(r.x) >= S) {
@@ -105,28 +102,22 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
                 cell[g] = w;
             }
         }
-        float lO = 0.f, lG = 0.f, lH = 0.f;
+        float tO = O, tG = Gv, tH = H;
         if (diffuse) {
             const int64_t xm = g - 1, xp = g + 1, ym = g - L, yp = g + L, zm = g - LL, zp = g + LL;
-            lO = (ld(iO + xm) + ld(iO + xp) + ld(iO + ym) + ld(iO + yp) + ld(iO + zm) + ld(iO + zp)) - 6.f * O;
-            lG = (ld(iG + xm) + ld(iG + xp) + ld(iG + ym) + ld(iG + yp) + ld(iG + zm) + ld(iG + zp)) - 6.f * Gv;
-            lH = (ld(iH + xm) + ld(iH + xp) + ld(iH + ym) + ld(iH + yp) + ld(iH + zm) + ld(iH + zp)) - 6.f * H;
+            tO = stencil_t(O, ld(iO + xm), ld(iO + xp), ld(iO + ym), ld(iO + yp), ld(iO + zm), ld(iO + zp), P.lam[0]);
+            tG = stencil_t(Gv, ld(iG + xm), ld(iG + xp), ld(iG + ym), ld(iG + yp), ld(iG + zm), ld(iG + zp),
+                           P.lam[1]);
+            tH = stencil_t(H, ld(iH + xm), ld(iH + xp), ld(iH + ym), ld(iH + yp), ld(iH + zm), ld(iH + zp), P.lam[2]);
         }
         float uO = 0.f, uG = 0.f, pH = 0.f;
         // uptake follows the kind after irradiation: a DOOMED cell keeps consuming,
         // an immediately killed one (variant switch) does not
         const uint32_t kr = w & kKindMask;
-        if (react && kr != kEmpty) {
-            const float f = (kr == kQ) ? P.f_Q : 1.f;
-            uO = f * P.q_O * O / (O + P.K_O);
-            const float gg = f * P.q_G * Gv / (Gv + P.K_G);
-            const float wa = P.O_an / (O + P.O_an);
-            uG = gg * (1.f + (P.k_an - 1.f) * wa);
-            pH = P.q_H * gg * P.k_an * wa;
-        }
-        oO[g] = cvt<T>(fmaxf(O + P.lam[0] * lO - uO, 0.f));
-        oG[g] = cvt<T>(fmaxf(Gv + P.lam[1] * lG - uG, 0.f));
-        oH[g] = cvt<T>(fmaxf(H + P.lam[2] * lH + pH, 0.f));
+        if (react && kr != kEmpty) uptake(kr, O, Gv, P, uO, uG, pH);
+        oO[g] = cvt<T>(fmaxf(__fsub_rn(tO, uO), 0.f));
+        oG[g] = cvt<T>(fmaxf(__fsub_rn(tG, uG), 0.f));
+        oH[g] = cvt<T>(fmaxf(__fadd_rn(tH, pH), 0.f));
     }
 }
 
@@ -158,34 +149,8 @@ __global__ void __launch_bounds__(kThreads) k_cell(const Block* __restrict__ blo
         if (i < b.n) {
             g = pr.site0 + b.begin + i;
             const uint32_t w = cell[g];
-            uint32_t kind = w & kKindMask;
-            if (kind != kEmpty) {
-                const uint32_t doomed = w & kDoomed;
-                uint32_t age = w >> kAgeShift;
-                const float O = ld(O_ + g), Gv = ld(G_ + g), H = ld(H_ + g);
-                uint32_t nw;
-                if ((P.flags & kFDeath) && (Gv < P.G_d || H > P.H_d)) {
-                    nw = kEmpty;
-                } else if (kind == kQ) {
-                    nw = w;
-                    if ((P.flags & kFQuiescence) && O >= P.O_q && Gv >= P.G_q && H <= P.H_q) nw = kG1 | doomed;
-                } else if (kind == kG1 && (P.flags & kFQuiescence) && (O < P.O_q || Gv < P.G_q || H > P.H_q)) {
-                    nw = kQ | doomed;
-                } else {
-                    age += 1;
-                    if (age >= (uint32_t)P.dur[kind - 1]) {
-                        if (kind < kM) {
-                            kind += 1;
-                            age = 0;
-                        } else if (doomed) {
-                            kind = kEmpty;  // mitotic catastrophe
-                        } else {
-                            age = (uint32_t)P.dur[kM - 1];
-                            want = (P.flags & kFDivision) != 0;
-                        }
-                    }
-                    nw = (kind == kEmpty) ? kEmpty : (kind | doomed | (age << kAgeShift));
-                }
+            if ((w & kKindMask) != kEmpty) {
+                const uint32_t nw = update_cell(w, ld(O_ + g), ld(G_ + g), ld(H_ + g), P, want);
                 if (nw != w) cell[g] = nw;
             }
         }

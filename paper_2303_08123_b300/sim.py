@@ -45,7 +45,8 @@ class SimConfig(ctypes.Structure):
         ("params", SimParams), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
         ("regrowth_h", ctypes.c_int32), ("t_end_steps", ctypes.c_int64), ("n_max_fitness", ctypes.c_double),
         ("dose_cap_gy", ctypes.c_double), ("hours", ctypes.c_int32), ("max_fractions", ctypes.c_int32),
-        ("init_word", ctypes.c_uint32), ("use_graphs", ctypes.c_int32),
+        ("init_word", ctypes.c_uint32), ("use_graphs", ctypes.c_int32), ("path", ctypes.c_int32),
+        ("tile_shape", ctypes.c_int32), ("z_chunk", ctypes.c_int32),
     ]
 
 
@@ -87,6 +88,7 @@ SIGNATURES = {
     "sim_save_state": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
     "sim_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "sim_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _i64p]),
+    "sim_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_int), _f64p]),
     "sim_diffuse_noalloc": (ctypes.c_int, [_P(SimConfig), ctypes.c_int, ctypes.c_int64, ctypes.c_double, _vp, _vp,
                                            _vp, _vp, _vp]),
     "sim_last_error": (ctypes.c_char_p, [_vp]),
@@ -122,7 +124,7 @@ def _ptr(a, ct):
 def make_config(params: Params = P0, seed: int = 0x5EED, precision="fp32", regrowth_h: int = 120,
                 t_end_steps: int = 0, n_max_fitness: float = 1500.0, dose_cap_gy: float = 30.0,
                 hours: int = 0, max_fractions: int = 240, init_word: int = 0xFFFFFFFF,
-                use_graphs: bool = True) -> SimConfig:
+                use_graphs: bool = True, path: str = "fused", tile_shape: int = 0, z_chunk: int = 0) -> SimConfig:
     c = SimConfig()
     c.params = pack_params(params)
     c.seed = seed
@@ -135,6 +137,9 @@ def make_config(params: Params = P0, seed: int = 0x5EED, precision="fp32", regro
     c.max_fractions = max_fractions
     c.init_word = init_word
     c.use_graphs = int(use_graphs)
+    c.path = {"fused": 0, "substep": 1}[path] if isinstance(path, str) else int(path)
+    c.tile_shape = tile_shape
+    c.z_chunk = z_chunk
     return c
 
 
@@ -247,6 +252,14 @@ class Simulator:
         nl = np.zeros(4, dtype=np.int64)
         self._call("sim_profile_steps", int(n_steps), _ptr(ms, ctypes.c_double), _ptr(nl, ctypes.c_int64))
         return ms, nl
+
+    def autotune(self, n_steps: int = 10):
+        """Time every fused tile shape on this batch, keep the fastest and re-seed
+        the batch at step 0.  Returns (best shape, ms per step per shape)."""
+        best = ctypes.c_int(0)
+        ms = np.full(4, -1.0)
+        self._call("sim_autotune", int(n_steps), ctypes.byref(best), _ptr(ms, ctypes.c_double))
+        return best.value, ms
 
     def save_state(self) -> bytes:
         size = ctypes.c_size_t(0)

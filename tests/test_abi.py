@@ -44,9 +44,9 @@ def test_workspace_size_validation(lib):
     L = np.array([40, 64], dtype=np.int32)
     Lp = L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     assert lib.sim_workspace_size(ctypes.byref(cfg), 2, Lp, ctypes.byref(size)) == 0
-    # 2 x 3 FP32 fields (24) + cell (4) + claim (8) + work list (8) = 44 B per site, plus tables
+    # 2 x 3 FP32 fields (24) + 2 cell words (8) + claim (8) + work list (8) = 48 B per site, plus tables
     sites = 40 ** 3 + 64 ** 3
-    assert 44 * sites <= size.value <= 44 * sites + 2_000_000
+    assert 48 * sites <= size.value <= 48 * sites + 2_000_000
     bad = np.array([7], dtype=np.int32)
     assert lib.sim_workspace_size(ctypes.byref(cfg), 1, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   ctypes.byref(size)) == -1

@@ -211,3 +211,63 @@ def test_division_claims_resolve_like_oracle_under_contention(cuda, orc):
     st = par.oracle_state(orc, L, f, cell)
     orc.step(p, st, SEED, 0, 12345)
     assert np.array_equal(sim.get_state(0)[3], st.cell)
+
+
+@pytest.mark.parametrize("shape,zc", [(1, 0), (2, 0), (2, 9), (1, 16), (3, 0), (4, 0), (3, 11)])
+def test_fused_path_equals_substep_path(cuda, shape, zc):
+    """The temporally blocked path (any tile shape, any z split) reproduces the
+    one-kernel-per-substep path bit for bit in FP32: same expressions, same order."""
+    from paper_2303_08123_b300 import csr
+    from synth import workloads
+    L, R = [40, 24, 33], [6, 5, 4]
+    prot = csr([workloads.daily_fractions(3, 2.5, 0.5), ([4.0], [0.5]), ([1.0, 3.0], [1.0, 0.5])])
+    out = []
+    for kw in (dict(path="substep"), dict(path="fused", tile_shape=shape, z_chunk=zc)):
+        sim = _sim(L, R, hours=2, t_end_steps=1500, **kw)
+        sim.load_protocols(*prot)
+        sim.run(0)
+        out.append(([sim.get_state(p) for p in range(3)], sim.counts(), sim.delivered_dose()))
+        sim.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("n_sub", [1, 3, 4])
+def test_fused_pass_split_matches_oracle(cuda, orc, n_sub):
+    """n_sub split into fused passes of two (and one) substeps: one step from a
+    crowded state against the oracle."""
+    L, step = 24, 900
+    p = P0.replace(n_sub=n_sub)
+    sim = _sim([L], [-1], params=p)
+    _load_single_fraction(sim, step, [2.0])
+    fields, cell = par.random_state(L, 31)
+    sim.set_state(0, *fields, cell)
+    sim.set_clock(step)
+    sim.run(1)
+    st = par.oracle_state(orc, L, fields, cell)
+    near, _ = orc.step(p, st, SEED, 0, step, dose=2.0)
+    g = sim.get_state(0)
+    r = par.compare(L, g[:3], g[3], st, near)
+    assert r["field_err"] <= par.FIELD_TOL and r["unexplained"] == 0, r
+
+
+def test_autotune_picks_a_shape_and_restarts_the_batch(cuda):
+    from paper_2303_08123_b300 import csr
+    L, R = [32, 32], [5, 6]
+    prot = csr([([2.0], [0.5]), ([1.0], [1.0])])
+    ref = _sim(L, R, hours=1, t_end_steps=900, tile_shape=1)
+    ref.load_protocols(*prot)
+    ref.run(0)
+    sim = _sim(L, R, hours=1, t_end_steps=900)
+    sim.load_protocols(*prot)
+    best, ms = sim.autotune(3)
+    assert best in (1, 2, 3, 4) and ms[best - 1] == ms[ms > 0].min()
+    assert sim.clock()[0][0] == 0
+    sim.run(0)
+    for p in range(2):
+        for x, y in zip(sim.get_state(p), ref.get_state(p)):
+            assert np.array_equal(x, y)
+    assert np.array_equal(sim.counts(), ref.counts())
