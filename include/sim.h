@@ -69,7 +69,8 @@ typedef struct {
     double dose_cap_gy;     /* reject protocols whose total dose exceeds this */
     int32_t hours;          /* hourly counts kept per protocol for hours 0..hours */
     int32_t max_fractions;  /* capacity of each protocol's fraction table */
-    uint32_t init_word;     /* Philox protocol word of the seeded spheroid */
+    uint32_t init_word;     /* Philox protocol word of the seeded spheroid; 0xFFFFFFFE: each
+                               slot seeds its own spheroid with its slot index */
     int32_t use_graphs;     /* 1: replay each simulated hour as one CUDA graph */
     int32_t path;           /* SIM_PATH_FUSED (default) or SIM_PATH_SUBSTEP */
     int32_t tile_shape;     /* fused tile: 0 auto; 1 = 32 x 16, 2 = 16 x 16 with two columns per
@@ -137,6 +138,12 @@ sim_status sim_fitness(sim_ctx* ctx, int32_t* out_count, double* out_fitness);
 /* Hourly live counts (host, n x (hours+1), row-major; -1 where the hour lies
  * beyond the protocol's horizon or has not been reached).  Synchronises. */
 sim_status sim_counts(sim_ctx* ctx, int32_t* out, int hours);
+
+/* Total substrate per protocol and field (sum over all L^3 sites of O2,
+ * glucose and H+ in mM, row-major n x 3): out64 summed in FP64 on the device,
+ * out32 in FP32 with Kahan compensation; either may be NULL.  Deterministic
+ * (blocks are added in a fixed order).  Synchronises. */
+sim_status sim_field_totals(sim_ctx* ctx, double* out64, float* out32);
 
 /* Delivered dose per protocol in Gy (host, n entries, FP64).  Synchronises. */
 sim_status sim_delivered_dose(sim_ctx* ctx, double* out);

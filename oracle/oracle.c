@@ -463,7 +463,9 @@ static void* batch_worker(void* arg) {
         or_stats tot;
         int32_t* cnt = J->counts ? J->counts + (int64_t)p * (J->hours + 1) : NULL;
         int nf = J->off[p + 1] - J->off[p];
-        int64_t T = run_impl(J->P, L, J->R[p], J->key, J->p_word[p], J->init_word, nf, J->dose + J->off[p],
+        /* init word 0xFFFFFFFE: every protocol grows its own spheroid (init word = its protocol word) */
+        const uint32_t iw = J->init_word == 0xFFFFFFFEu ? J->p_word[p] : J->init_word;
+        int64_t T = run_impl(J->P, L, J->R[p], J->key, J->p_word[p], iw, nf, J->dose + J->off[p],
                              J->wait + J->off[p], J->t_end, J->regrowth_h, J->max_steps, cnt, J->hours, f,
                              f + N, f + 2 * N, cell, NULL, &tot);
         J->n_final[p] = tot.n_live;

@@ -81,7 +81,8 @@ int64_t or_run(const or_params* P, int L, int R, const uint32_t key[2], uint32_t
 
 /* Many protocols on n_threads host threads (one protocol per thread at a time).
  * Per protocol p: lattice L[p], radius R[p], fractions off[p]..off[p+1]-1,
- * protocol word p_word[p].  Outputs: final live count n_final[p], steps[p] and
+ * protocol word p_word[p]; init_word 0xFFFFFFFE seeds each protocol's spheroid
+ * with its own protocol word.  Outputs: final live count n_final[p], steps[p] and
  * (nullable) counts[p*(hours+1) + h].  max_steps > 0 stops every run after that
  * many steps (used to time a bounded sample).  Returns 0. */
 int or_run_batch(const or_params* P, int n, const int32_t* L, const int32_t* R,

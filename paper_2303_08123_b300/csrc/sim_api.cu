@@ -31,7 +31,7 @@ size_t elem_size(int precision) { return precision == SIM_FP32 ? 4 : 2; }
 // Byte offsets of every region of the workspace.
 struct Layout {
     size_t proto, blocks, tiles, fstep, fdose, field[2][3], cell[2], claim, intents, target, icount, counts, cum,
-        clock, status, final_count, total;
+        clock, status, final_count, first_block, part64, part32, tot64, tot32, total;
 };
 
 Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks, int64_t ntiles) {
@@ -62,6 +62,11 @@ Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nb
     l.clock = take(sizeof(int64_t));
     l.status = take(sizeof(uint32_t));
     l.final_count = take(sizeof(int32_t) * n);
+    l.first_block = take(sizeof(int32_t) * (n + 1));
+    l.part64 = take(sizeof(double) * 3 * nblocks);
+    l.part32 = take(sizeof(float) * 3 * nblocks);
+    l.tot64 = take(sizeof(double) * 3 * n);
+    l.tot32 = take(sizeof(float) * 3 * n);
     l.total = off;
     return l;
 }
@@ -369,7 +374,7 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, in
     int buf = start_buf;
     if (ev) cudaEventRecord(ev[0], s);
     for (int sub = 0; sub < c->P.n_sub; ++sub) {
-        k_substep<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, sub == 0, (const T*)c->field(buf, 0),
+        k_substep<T><<<nb, kThreads, 0, s>>>(blocks, protos, clock, k_off, sub, (const T*)c->field(buf, 0),
                                              (const T*)c->field(buf, 1), (const T*)c->field(buf, 2),
                                              (T*)c->field(buf ^ 1, 0), (T*)c->field(buf ^ 1, 1),
                                              (T*)c->field(buf ^ 1, 2), cell, c->at<int64_t>(c->lay.fstep),
@@ -498,6 +503,29 @@ size_t ckpt_bytes(const sim_ctx* c) {
 
 }  // namespace
 
+namespace {
+
+template <typename T>
+void launch_totals(sim_ctx* c) {
+    k_totals_part<T><<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
+        c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), (const T*)c->field(c->cur, 0),
+        (const T*)c->field(c->cur, 1), (const T*)c->field(c->cur, 2), c->at<double>(c->lay.part64),
+        c->at<float>(c->lay.part32));
+}
+
+// Switch the fused work list to tile shape `sh` (rebuilds and uploads the tiles; drops captured graphs).
+sim_status set_shape(sim_ctx* c, int sh, const std::vector<int32_t>& L) {
+    c->shape = sh;
+    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh);
+    drop_graphs(c);
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "set shape");
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sim_status_string(sim_status s) {
@@ -595,8 +623,13 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
         nt = t > nt ? t : nt;
     }
     c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size(), nt);
+    std::vector<int32_t> first_block(n + 1, 0);
+    for (size_t b = 0; b < c->blocks.size(); ++b) first_block[c->blocks[b].p + 1] = (int32_t)(b + 1);
     cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.blocks, c->blocks.data(), sizeof(Block) * c->blocks.size(),
                                     cudaMemcpyHostToDevice, c->stream);
+    if (!e)
+        e = cudaMemcpyAsync(c->ws + c->lay.first_block, first_block.data(), sizeof(int32_t) * (n + 1),
+                            cudaMemcpyHostToDevice, c->stream);
     if (!e)
         e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
                             cudaMemcpyHostToDevice, c->stream);
@@ -746,17 +779,6 @@ sim_status sim_profile_steps(sim_ctx* c, int n_steps, double* ms, int64_t* launc
     return st;
 }
 
-// Switch the fused work list to tile shape `sh` (rebuilds and uploads the tiles; drops captured graphs).
-sim_status set_shape(sim_ctx* c, int sh, const std::vector<int32_t>& L) {
-    c->shape = sh;
-    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh);
-    drop_graphs(c);
-    cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
-                                    cudaMemcpyHostToDevice, c->stream);
-    if (!e) e = cudaStreamSynchronize(c->stream);
-    return cuda_check(c, e, "set shape");
-}
-
 sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     if (!c || n_steps < 1) return SIM_EINVAL;
     if (!c->loaded) return fail(c, SIM_ESTATE, "load protocols before autotuning");
@@ -803,6 +825,26 @@ sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     if (!st) st = reset_device(c);  // the timing steps advanced the batch: start it again from step 0
     if (!st) st = read_status(c);
     return st;
+}
+
+sim_status sim_field_totals(sim_ctx* c, double* out64, float* out32) {
+    if (!c) return SIM_EINVAL;
+    switch (c->cfg.precision) {
+        case SIM_BF16: launch_totals<__nv_bfloat16>(c); break;
+        case SIM_FP16: launch_totals<__half>(c); break;
+        default: launch_totals<float>(c); break;
+    }
+    k_totals_finish<<<(3 * c->n + 127) / 128, 128, 0, c->stream>>>(
+        c->at<int32_t>(c->lay.first_block), c->n, c->at<double>(c->lay.part64), c->at<float>(c->lay.part32),
+        c->at<double>(c->lay.tot64), c->at<float>(c->lay.tot32));
+    if (sim_status st = cuda_check(c, cudaGetLastError(), "totals launch")) return st;
+    cudaError_t e = cudaSuccess;
+    if (out64) e = cudaMemcpyAsync(out64, c->ws + c->lay.tot64, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost,
+                                   c->stream);
+    if (!e && out32)
+        e = cudaMemcpyAsync(out32, c->ws + c->lay.tot32, sizeof(float) * 3 * c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e) return cuda_check(c, e, "totals copy");
+    return read_status(c);
 }
 
 sim_status sim_fitness(sim_ctx* c, int32_t* out_count, double* out_fitness) {
@@ -1097,7 +1139,7 @@ extern "C" sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t 
     for (int sub = 0; sub < P.n_sub; ++sub) {
         k_substep<float><<<(unsigned)blocks.size(), kThreads, 0, s>>>(
             (const Block*)(base + kNaBlocks), (const Proto*)(base + kNaProto), (const int64_t*)(base + kNaClock), 0,
-            sub == 0, buf[cur][0], buf[cur][1], buf[cur][2], buf[cur ^ 1][0], buf[cur ^ 1][1], buf[cur ^ 1][2], cell,
+            sub, buf[cur][0], buf[cur][1], buf[cur][2], buf[cur ^ 1][0], buf[cur ^ 1][1], buf[cur ^ 1][2], cell,
             (const int64_t*)(base + kNaFstep), (const double*)(base + kNaFdose), (double*)(base + kNaCum), P);
         cur ^= 1;
     }

@@ -99,6 +99,42 @@ __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float v) { return __
 template <>
 __device__ __forceinline__ __half cvt<__half>(float v) { return __float2half_rn(v); }
 
+// Stochastic rounding for 2-byte field storage.  Round-to-nearest loses every
+// per-substep increment below half an ulp of the stored value (a BF16 ulp of
+// 0.28 mM is 1e-3 mM, above the O2 uptake of one substep), so the fields
+// stagnate.  Rounding up with probability equal to the remainder keeps the
+// stored value unbiased.  The random bits come from a counter-based integer
+// hash of (site, step, salt), so runs remain reproducible.
+__device__ __forceinline__ uint32_t dither_bits(uint32_t site, uint32_t step, uint32_t salt) {
+    uint32_t x = site * 0x9E3779B1u ^ (step + 0x632BE5ABu) * 0x85EBCA77u ^ salt * 0xC2B2AE3Du;
+    x ^= x >> 16;  // integer avalanche: alternating xor-shifts and odd multiplications
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T cvt_sr(float v, uint32_t r);
+template <>
+__device__ __forceinline__ float cvt_sr<float>(float v, uint32_t) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_sr<__nv_bfloat16>(float v, uint32_t r) {
+    // BF16 keeps the top 16 bits of an FP32: adding 16 random low bits before truncation rounds up with
+    // probability (dropped bits) / 2^16 (values here are finite and >= 0)
+    const uint32_t b = __float_as_uint(v) + (r & 0xFFFFu);
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+template <>
+__device__ __forceinline__ __half cvt_sr<__half>(float v, uint32_t r) {
+    const __half lo = __float2half_rd(v), hi = __float2half_ru(v);
+    const float flo = __half2float(lo), fhi = __half2float(hi);
+    if (fhi == flo) return lo;
+    const float u = (float)(r >> 8) * 0x1p-24f;  // uniform in [0, 1)
+    return (u < (v - flo) / (fhi - flo)) ? hi : lo;
+}
+
 __device__ __forceinline__ bool is_face(int L, int x, int y, int z) {
     return x == 0 || y == 0 || z == 0 || x == L - 1 || y == L - 1 || z == L - 1;
 }

@@ -42,19 +42,20 @@ struct FusedShape {
     static_assert(HX % 2 == 0, "the halo row must hold whole column pairs");
 };
 
+// store a column pair; 2-byte types round stochastically with the bits ra, rb
 template <typename T>
-__device__ __forceinline__ void st_pair(T* p, float2 v, bool vec, bool sa, bool sb) {
+__device__ __forceinline__ void st_pair(T* p, float2 v, bool vec, bool sa, bool sb, uint32_t ra, uint32_t rb) {
     if (vec) {
         if constexpr (sizeof(T) == 4) {
             *reinterpret_cast<float2*>(p) = v;
         } else {
-            T pair[2] = {cvt<T>(v.x), cvt<T>(v.y)};
+            T pair[2] = {cvt_sr<T>(v.x, ra), cvt_sr<T>(v.y, rb)};
             *reinterpret_cast<uint32_t*>(p) = *reinterpret_cast<uint32_t*>(pair);
         }
         return;
     }
-    if (sa) p[0] = cvt<T>(v.x);
-    if (sb) p[1] = cvt<T>(v.y);
+    if (sa) p[0] = cvt_sr<T>(v.x, ra);
+    if (sb) p[1] = cvt_sr<T>(v.y, rb);
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -329,9 +330,21 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
                     const bool sa = oa && !fa && !zface, sb = ob && !fb && !zface;  // interior sites written
                     const bool vw = vec && sa && sb;
                     if (sa || sb) {
-                        st_pair(oO + pr.site0 + col + o, v[0], vw, sa, sb);
-                        st_pair(oG + pr.site0 + col + o, v[1], vw, sa, sb);
-                        st_pair(oH + pr.site0 + col + o, v[2], vw, sa, sb);
+                        // stochastic-rounding bits per (site, step, pass, field); the substep path uses
+                        // salts 3 * substep + field, a fused pass 3 * (its last substep) + field
+                        uint32_t r[6] = {0, 0, 0, 0, 0, 0};
+                        if constexpr (sizeof(T) != 4) {
+                            const uint32_t ga = (uint32_t)(pr.site0 + col + o), stp = (uint32_t)step;
+                            const uint32_t salt = 3u * (EPI ? (uint32_t)P.n_sub - 1u : (uint32_t)K - 1u) + 100u;
+#pragma unroll
+                            for (int f = 0; f < 3; ++f) {
+                                r[2 * f] = dither_bits(ga, stp, salt + f);
+                                r[2 * f + 1] = dither_bits(ga + 1, stp, salt + f);
+                            }
+                        }
+                        st_pair(oO + pr.site0 + col + o, v[0], vw, sa, sb, r[0], r[1]);
+                        st_pair(oG + pr.site0 + col + o, v[1], vw, sa, sb, r[2], r[3]);
+                        st_pair(oH + pr.site0 + col + o, v[2], vw, sa, sb, r[4], r[5]);
                     }
                     const uint2 w0 = wr[sq];
                     uint32_t* pc = cout + pr.site0 + col + o;

@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(kThreads) k_init(const Block* __restrict__ blo
         uint32_t w = kEmpty;
         const int dx = x - c, dy = y - c, dz = z - c;
         if (!is_face(L, x, y, z) && pr.R >= 0 && dx * dx + dy * dy + dz * dz <= pr.R * pr.R) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)s, 0u, kPurposeInit, P.init_word), P.key0, P.key1);
+            // init word 0xFFFFFFFE: every slot grows its own spheroid (init word = slot index)
+            const uint32_t iw = P.init_word == 0xFFFFFFFEu ? (uint32_t)b.p : P.init_word;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)s, 0u, kPurposeInit, iw), P.key0, P.key1);
             const uint32_t kind = 1u + pick24(r.x, 4u);
             const uint32_t age = pick24(r.y, (uint32_t)P.dur[kind - 1]);
             w = kind | (age << kAgeShift);
@@ -53,13 +55,13 @@ __global__ void __launch_bounds__(kThreads) k_init(const Block* __restrict__ blo
 // Uptake of a cell with weight f (1 cycling, f_Q quiescent):
 //   U_O = f q_O O/(O+K_O);  g = f q_G G/(G+K_G);  w = O_an/(O+O_an)
 //   U_G = g (1 + (k_an-1) w);  H+ release = q_H g k_an w.
-// Faces are Dirichlet (medium) and are never written.  With `first`, the
+// Faces are Dirichlet (medium) and are never written.  In substep 0 the
 // step's dose fraction is applied before diffusion from the step-start O2:
 // survival S = exp(-a D - b D^2), a = alpha phi OMF(O), b = beta (phi OMF)^2,
 // OMF(O) = (m O + K)/(m (O + K)); a cell with Philox uniform u >= S is DOOMED.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ blocks, const Proto* __restrict__ protos,
-                                                      const int64_t* __restrict__ clock, int k_off, int first,
+                                                      const int64_t* __restrict__ clock, int k_off, int sub,
                                                       const T* __restrict__ iO, const T* __restrict__ iG,
                                                       const T* __restrict__ iH, T* __restrict__ oO, T* __restrict__ oG,
                                                       T* __restrict__ oH, uint32_t* __restrict__ cell,
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
     const int64_t step = *clock + k_off;
     if (step >= pr.t_end) return;
     float dose = 0.f;
-    if (first) {
+    if (sub == 0) {  // the step's fraction is applied in its first substep
         __shared__ float s_dose;
         if (threadIdx.x == 0) {
             const double d = dose_at(pr, fstep, fdose, step);
@@ -115,9 +117,12 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
         // an immediately killed one (variant switch) does not
         const uint32_t kr = w & kKindMask;
         if (react && kr != kEmpty) uptake(kr, O, Gv, P, uO, uG, pH);
-        oO[g] = cvt<T>(fmaxf(__fsub_rn(tO, uO), 0.f));
-        oG[g] = cvt<T>(fmaxf(__fsub_rn(tG, uG), 0.f));
-        oH[g] = cvt<T>(fmaxf(__fadd_rn(tH, pH), 0.f));
+        // stochastic-rounding bits per (site, step, substep, field); unused with FP32 storage
+        const bool sr = sizeof(T) != 4;
+        const uint32_t salt = 3u * (uint32_t)sub;
+        oO[g] = cvt_sr<T>(fmaxf(__fsub_rn(tO, uO), 0.f), sr ? dither_bits((uint32_t)g, (uint32_t)step, salt) : 0u);
+        oG[g] = cvt_sr<T>(fmaxf(__fsub_rn(tG, uG), 0.f), sr ? dither_bits((uint32_t)g, (uint32_t)step, salt + 1) : 0u);
+        oH[g] = cvt_sr<T>(fmaxf(__fadd_rn(tH, pH), 0.f), sr ? dither_bits((uint32_t)g, (uint32_t)step, salt + 2) : 0u);
     }
 }
 
@@ -280,5 +285,70 @@ __global__ void __launch_bounds__(kThreads) k_count(const Block* __restrict__ bl
 }
 
 __global__ void k_tick(int64_t* clock, int64_t by) { *clock += by; }
+
+// ---------------------------------------------------------------------------
+// Field totals per protocol (substrate mass): each work-list block reduces its
+// sites in FP64 and, separately, in FP32 with Kahan compensation per thread;
+// k_totals_finish then adds the blocks of each protocol in order (FP64, and
+// FP32 Kahan), so the result does not depend on scheduling.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_totals_part(const Block* __restrict__ blocks,
+                                                          const Proto* __restrict__ protos, const T* __restrict__ O_,
+                                                          const T* __restrict__ G_, const T* __restrict__ H_,
+                                                          double* __restrict__ part64, float* __restrict__ part32) {
+    const Block b = blocks[blockIdx.x];
+    const Proto pr = protos[b.p];
+    const T* f[3] = {O_, G_, H_};
+    __shared__ double s64[3][kThreads];
+    __shared__ float s32[3][kThreads];
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        float sum = 0.f, comp = 0.f;  // Kahan: sum + comp carries the low-order bits
+        for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
+            const float v = ld(f[k] + pr.site0 + b.begin + i);
+            acc += (double)v;
+            const float yk = __fsub_rn(v, comp);
+            const float t = __fadd_rn(sum, yk);
+            comp = __fsub_rn(__fsub_rn(t, sum), yk);
+            sum = t;
+        }
+        s64[k][threadIdx.x] = acc;
+        s32[k][threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int k = threadIdx.x;
+        double a = 0.0;
+        float sum = 0.f, comp = 0.f;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            a += s64[k][t];
+            const float yk = __fsub_rn(s32[k][t], comp);
+            const float tt = __fadd_rn(sum, yk);
+            comp = __fsub_rn(__fsub_rn(tt, sum), yk);
+            sum = tt;
+        }
+        part64[(size_t)blockIdx.x * 3 + k] = a;
+        part32[(size_t)blockIdx.x * 3 + k] = sum;
+    }
+}
+
+__global__ void k_totals_finish(const int32_t* __restrict__ first_block, int n, const double* __restrict__ part64,
+                                const float* __restrict__ part32, double* __restrict__ out64,
+                                float* __restrict__ out32) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 3 * n) return;
+    const int p = idx / 3, k = idx % 3;
+    double a = 0.0;
+    float sum = 0.f, comp = 0.f;
+    for (int b = first_block[p]; b < first_block[p + 1]; ++b) {
+        a += part64[(size_t)b * 3 + k];
+        const float yk = __fsub_rn(part32[(size_t)b * 3 + k], comp);
+        const float t = __fadd_rn(sum, yk);
+        comp = __fsub_rn(__fsub_rn(t, sum), yk);
+        sum = t;
+    }
+    out64[idx] = a;
+    out32[idx] = sum;
+}
 
 }  // namespace simdev

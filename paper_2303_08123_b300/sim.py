@@ -81,6 +81,7 @@ SIGNATURES = {
     "sim_fitness": (ctypes.c_int, [_vp, _i32p, _f64p]),
     "sim_counts": (ctypes.c_int, [_vp, _i32p, ctypes.c_int]),
     "sim_delivered_dose": (ctypes.c_int, [_vp, _f64p]),
+    "sim_field_totals": (ctypes.c_int, [_vp, _f64p, _f32p]),
     "sim_clock": (ctypes.c_int, [_vp, _i64p, _i64p]),
     "sim_set_clock": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "sim_get_state": (ctypes.c_int, [_vp, ctypes.c_int, _f32p, _f32p, _f32p, _u32p]),
@@ -217,6 +218,13 @@ class Simulator:
         out = np.zeros(self.n * (h + 1), dtype=np.int32)
         self._call("sim_counts", _ptr(out, ctypes.c_int32), h)
         return out.reshape(self.n, h + 1)
+
+    def field_totals(self):
+        """(FP64 totals, Kahan FP32 totals), each n x 3 (O2, glucose, H+) in mM summed over sites."""
+        a = np.zeros(self.n * 3, dtype=np.float64)
+        b = np.zeros(self.n * 3, dtype=np.float32)
+        self._call("sim_field_totals", _ptr(a, ctypes.c_double), _ptr(b, ctypes.c_float))
+        return a.reshape(self.n, 3), b.reshape(self.n, 3)
 
     def delivered_dose(self):
         out = np.zeros(self.n, dtype=np.float64)

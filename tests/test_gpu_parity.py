@@ -271,3 +271,25 @@ def test_autotune_picks_a_shape_and_restarts_the_batch(cuda):
         for x, y in zip(sim.get_state(p), ref.get_state(p)):
             assert np.array_equal(x, y)
     assert np.array_equal(sim.counts(), ref.counts())
+
+
+def test_full_size_batch_in_bench_configuration(cuda, orc):
+    """The bench's launch configuration (256 protocols x 64^3, autotuned fused
+    path, one hour graph): sampled protocols equal the oracle after 600 steps."""
+    from paper_2303_08123_b300 import Simulator, csr
+    from synth import workloads
+    prot = workloads.ga_batch(256, seed=2)
+    prot[0] = ([2.0] + prot[0][0][1:], [0.5] + prot[0][1][1:])  # a fraction inside the hour for slot 0
+    sim = Simulator([64] * 256, [8] * 256, seed=SEED, hours=2, dose_cap_gy=20.0)
+    sim.load_protocols(*csr(prot))
+    sim.autotune(3)
+    sim.run(600)
+    for p in (0, 131, 255):
+        d, w = prot[p]
+        ref = orc.run(P0, 64, 8, SEED, p, d, w, t_end_steps=600, hours=1)
+        O, G, H, cell = sim.get_state(p)
+        assert ref["stats"]["n_near"] == 0 or np.array_equal(cell, ref["state"].cell)
+        assert np.array_equal(cell, ref["state"].cell), (p, ref["stats"])
+        for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
+            assert np.max(np.abs(g - o)) / m < 1e-4
+        assert np.array_equal(sim.counts()[p][:2], ref["counts"][:2])
