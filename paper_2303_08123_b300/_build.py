@@ -21,6 +21,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 # one shared library per entry translation unit
 TARGETS = {
     "libsim.so": ["sim_api.cu"],
+    "libmlp.so": ["mlp_api.cu"],
 }
 
 

@@ -84,3 +84,18 @@ def test_binding_struct_layout_matches_header(tmp_path):
     assert vals[0] == ctypes.sizeof(SimConfig) and vals[1] == ctypes.sizeof(SimParams)
     assert vals[2:2 + len(fields)] == [getattr(SimConfig, f).offset for f in fields]
     assert vals[2 + len(fields):] == [getattr(SimParams, f).offset for f in pf]
+
+
+def test_mlp_library_exports_every_declared_symbol():
+    from paper_2303_08123_b300 import _build
+    _build.build()
+    from paper_2303_08123_b300.surrogate import SIGNATURES, load_library
+    lib = load_library()
+    names = declared("mlp.h")
+    assert {"mlp_create", "mlp_forward", "mlp_train_step", "mlp_gradients", "mlp_gemm_bf16"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n) and n in SIGNATURES, n
+    assert lib.mlp_num_params() == 256 * 48 + 256 + 2 * (256 * 256 + 256) + 256 + 1
+    size = ctypes.c_size_t()
+    assert lib.mlp_workspace_size(100, ctypes.byref(size)) == -1  # batches are multiples of 128
+    assert lib.mlp_workspace_size(256, ctypes.byref(size)) == 0 and size.value > 0
