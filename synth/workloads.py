@@ -74,15 +74,3 @@ def ragged_batch(n: int = 1024, seed: int = 3, r_min: int = 4, r_max: int = 20, 
         w = rng.choice(waits, size=k).tolist()
         protos.append((cap_total_dose(d, cap, dose_step), [float(x) for x in w]))
     return L, R.astype(np.int32), protos
-
-
-def protocol_features(protocols, max_frac: int = 15, dose_scale: float = 5.0, wait_scale: float = 60.0):
-    """Surrogate input: per fraction slot (dose / dose_scale, wait / wait_scale,
-    mask), zero-padded to max_frac slots: 3 * max_frac features."""
-    X = np.zeros((len(protocols), 3 * max_frac), dtype=np.float32)
-    for i, (d, w) in enumerate(protocols):
-        k = min(len(d), max_frac)
-        X[i, 0:3 * k:3] = np.asarray(d[:k]) / dose_scale
-        X[i, 1:3 * k:3] = np.asarray(w[:k]) / wait_scale
-        X[i, 2:3 * k:3] = 1.0
-    return X
