@@ -108,7 +108,7 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     a = ap.parse_args()
     setup = SimSetup(L=24, R=5, regrowth_h=6)
-    cfg = ga.GAConfig(n_slots=48, d_max=2.5, total_cap=8.0, min_gap=1, population=a.population,
+    cfg = ga.GAConfig(n_slots=48, d_max=2.5, total_cap=8.0, min_gap=4, population=a.population,
                       mutations=("swap", "split", "dose_time", "dose_value"), p_mut=0.5)
     rng = np.random.default_rng(a.seed)
     train = [ga.to_pairs(ga.random_protocol(cfg, rng)) for _ in range(a.train)]
