@@ -42,13 +42,34 @@ UNIT = "protocols/s"
 STEPS_PER_HOUR = 600
 
 
+WORKLOAD = "ga_batch"
+
+
 def workload():
-    prot = workloads.ga_batch(N_PROT, seed=2)
+    """(protocols, mean horizon in h, lattice sides, radii) of the benchmarked batch."""
+    if WORKLOAD == "ragged":
+        Ls, Rs, prot = workloads.ragged_batch(N_PROT, seed=3)
+    else:
+        prot = workloads.ga_batch(N_PROT, seed=2)
+        Ls, Rs = np.full(N_PROT, L, dtype=np.int32), np.full(N_PROT, R, dtype=np.int32)
     t_end_h = [sum(w) + 120.0 for _, w in prot]
-    return prot, float(np.mean(t_end_h))
+    return prot, float(np.mean(t_end_h)), Ls, Rs
 
 
 def workload_config(mean_t_end_h, precision="fp32"):
+    if WORKLOAD == "ragged":
+        _, _, Ls, _ = workload()
+        return {
+            "workload": f"ragged batch {N_PROT} protocols, spheroid radius uniform 4-20, lattice 16*ceil(5R/16) "
+                        f"(32^3-112^3, mean {float(np.mean(Ls.astype(np.float64) ** 3)):.0f} sites), "
+                        "5-15 fractions of {1..5} Gy, waits {6..60} h, cap 30 Gy, "
+                        f"{precision} fields, n_sub={P0.n_sub}",
+            "step": "one simulated hour (600 CA steps) of the whole batch",
+            "protocols_per_s": "protocol-steps/s divided by the mean horizon (last fraction + 120 h)",
+            "mean_horizon_h": round(mean_t_end_h, 2),
+            "l2": "working set > 126 MB L2: no flush needed",
+            "parallelism": "independent protocol batch per GPU, persistent tile scheduling",
+        }
     return {
         "workload": f"ga_batch {N_PROT} protocols x {L}^3 lattice, seeded spheroid R={R} (2109 cells), "
                     "10 fractions/protocol, doses {0.5..2.5} Gy, waits {6..60} h, cap 20 Gy, "
@@ -149,17 +170,17 @@ def cpu_baseline(mean_t_end_h, max_steps=None):
     number of steps each; extrapolated to whole protocols by the mean horizon."""
     import oracle
     cores = os.cpu_count() or 1
-    prot, _ = workload()
+    prot, _, Ls, Rs = workload()
     n = min(cores, N_PROT)
-    steps = max_steps or 1200
+    steps = max_steps or (1200 if WORKLOAD != "ragged" else 300)
     off, d, w = _csr(prot[:n])
     t0 = time.perf_counter()
-    res = oracle.run_batch(P0, [L] * n, [R] * n, SEED, off, d, w, max_steps=steps, n_threads=n)
+    res = oracle.run_batch(P0, Ls[:n], Rs[:n], SEED, off, d, w, max_steps=steps, n_threads=n)
     dt = time.perf_counter() - t0
-    site_steps = float(np.sum(res["steps"])) * L ** 3
-    per_protocol = mean_t_end_h * STEPS_PER_HOUR * L ** 3
+    site_steps = float(np.sum(res["steps"] * Ls[:n].astype(np.float64) ** 3))
+    per_protocol = mean_t_end_h * STEPS_PER_HOUR * float(np.mean(Ls.astype(np.float64) ** 3))
     return {"value": site_steps / dt / per_protocol, "unit": UNIT, "cores": n, "kind": "oracle",
-            "sample": f"{n} protocols x {steps} steps of the {L}^3 workload on {n} threads "
+            "sample": f"{n} protocols x {steps} steps of the benchmarked workload on {n} threads "
                       f"({dt:.1f} s); extrapolated by the {mean_t_end_h:.1f} h mean horizon",
             "site_steps_per_s": site_steps / dt}
 
@@ -169,7 +190,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    prot, mean_h = workload()
+    prot, mean_h, _, _ = workload()
     vals = []
     for _ in range(args.warmup):
         cpu_baseline(mean_h, max_steps=20)
@@ -201,7 +222,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prot, mean_h = workload()
+    prot, mean_h, Ls, Rs = workload()
     off, d, w = csr(prot)
     K, W = args.steps, args.warmup
     hours = W + K + 2
@@ -211,8 +232,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    sim = Simulator([L] * N_PROT, [R] * N_PROT, seed=SEED, precision=args.precision, hours=hours,
-                    dose_cap_gy=20.0, device=dev, path=args.path)
+    sim = Simulator(Ls, Rs, seed=SEED, precision=args.precision, hours=hours,
+                    dose_cap_gy=30.0, device=dev, path=args.path)
     sim.load_protocols(off, d, w)
     shape, shape_ms = sim.autotune(10) if args.path == "fused" else (0, None)  # re-seeds the batch at step 0
     stream = torch.cuda.current_stream(dev)
@@ -232,16 +253,16 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms = float(t.item())
     ms_per_step = ms / K
-    sites = N_PROT * L ** 3
+    sites = float(np.sum(Ls.astype(np.float64) ** 3))
     protocol_steps_per_s = world * N_PROT * STEPS_PER_HOUR * K / (ms / 1e3)
     value = protocol_steps_per_s / (mean_h * STEPS_PER_HOUR)
-    site_steps_per_s = protocol_steps_per_s * L ** 3
+    site_steps_per_s = world * sites * STEPS_PER_HOUR * K / (ms / 1e3)
     per_ca_step = ((P0.n_sub + 1) // 2 + 2) if args.path == "fused" else (P0.n_sub + 3)
     launches_per_step = STEPS_PER_HOUR * per_ca_step + 2  # passes (or substeps + cell), claim, resolve; tick, count
 
     # per-kernel device time over plain steps of the same batch (CUDA events on the launching stream)
     kms, kl = sim.profile_steps(60)
-    interior = (L - 2) ** 3 * N_PROT
+    interior = float(np.sum((Ls.astype(np.float64) - 2) ** 3))
     es = 4 if args.precision == "fp32" else 2
     if args.path == "fused":
         kn = "k_fused1" if shape in (3, 4) else "k_fused"
@@ -284,8 +305,8 @@ def run_ours(args):
     d2h = cnt.nbytes + fit.nbytes
 
     # plain form: one protocol at a time, per-step launches, no graph
-    plain = Simulator([L], [R], seed=SEED, precision=args.precision, use_graphs=False, dose_cap_gy=20.0,
-                      device=dev)
+    plain = Simulator(Ls[:1], Rs[:1], seed=SEED, precision=args.precision, use_graphs=False, dose_cap_gy=30.0,
+                      device=dev, path=args.path)
     po, pd, pw = csr(prot[:1])
     plain.load_protocols(po, pd, pw)
     plain.run(50)
@@ -295,7 +316,9 @@ def run_ours(args):
     plain.run(STEPS_PER_HOUR)
     b.record(stream)
     torch.cuda.synchronize()
-    plain_val = STEPS_PER_HOUR / (a.elapsed_time(b) / 1e3) / (mean_h * STEPS_PER_HOUR)
+    # the plain form evaluates protocols one after another: scale the first protocol's time by lattice volume
+    plain_val = STEPS_PER_HOUR / (a.elapsed_time(b) / 1e3) / (mean_h * STEPS_PER_HOUR) * \
+        float(Ls[0]) ** 3 / float(np.mean(Ls.astype(np.float64) ** 3))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -329,10 +352,13 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "substep"])
+    ap.add_argument("--workload", default="ga_batch", choices=["ga_batch", "ragged"],
+                    help="ga_batch: 256 x 64^3 (default); ragged: 1,024 protocols on 32^3-112^3")
     ap.add_argument("--protocols", type=int, default=256, help="batch size per GPU (smaller: profiling cases)")
     args = ap.parse_args()
-    global N_PROT
-    N_PROT = args.protocols
+    global N_PROT, WORKLOAD
+    WORKLOAD = args.workload
+    N_PROT = args.protocols if not (args.workload == "ragged" and args.protocols == 256) else 1024
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

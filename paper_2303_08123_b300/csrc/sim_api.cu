@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 #include <string>
@@ -31,7 +32,7 @@ size_t elem_size(int precision) { return precision == SIM_FP32 ? 4 : 2; }
 // Byte offsets of every region of the workspace.
 struct Layout {
     size_t proto, blocks, tiles, fstep, fdose, field[2][3], cell[2], claim, intents, target, icount, counts, cum,
-        clock, status, final_count, first_block, part64, part32, tot64, tot32, total;
+        clock, status, final_count, first_block, part64, part32, tot64, tot32, tile_ctr, total;
 };
 
 Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks, int64_t ntiles) {
@@ -67,6 +68,7 @@ Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nb
     l.part32 = take(sizeof(float) * 3 * nblocks);
     l.tot64 = take(sizeof(double) * 3 * n);
     l.tot32 = take(sizeof(float) * 3 * n);
+    l.tile_ctr = take(sizeof(uint32_t) * 2 * kMaxPasses);
     l.total = off;
     return l;
 }
@@ -142,6 +144,8 @@ std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int
                     t.push_back(e);
                 }
     }
+    // longest z ranges first, so the persistent CTAs finish together (ties keep their order)
+    std::stable_sort(t.begin(), t.end(), [](const Tile& a, const Tile& b) { return a.z1 - a.z0 > b.z1 - b.z0; });
     return t;
 }
 
@@ -234,6 +238,7 @@ sim_status reset_device(sim_ctx* c) {
     }
     if (st) return st;
     cudaError_t e = cudaMemsetAsync(c->ws + c->lay.icount, 0, 8, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.tile_ctr, 0, sizeof(uint32_t) * 2 * kMaxPasses, c->stream);
     if (!e)
         e = cudaMemsetAsync(c->ws + c->lay.counts, 0, sizeof(int32_t) * c->n * (size_t)(c->cfg.hours + 1), c->stream);
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.cum, 0, sizeof(double) * c->n, c->stream);
@@ -247,37 +252,57 @@ sim_status reset_device(sim_ctx* c) {
 }
 
 // One CA step for every protocol, reading the step index as clock + k_off.
+// Persistent grid: as many CTAs as fit on the device at once (at most one per tile).
+template <typename Kern>
+unsigned persistent_grid(Kern kern, int threads, size_t smem, size_t n_tiles) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    const size_t g = (size_t)sms * (size_t)(per_sm > 0 ? per_sm : 1);
+    return (unsigned)(g < n_tiles ? g : n_tiles);
+}
+
 template <typename T, int TX, int TY, int K, bool EPI>
-void launch_fused_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout) {
+void launch_fused_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
+                    int pass) {
     using Sh = FusedShape<TX, TY, K>;
-    k_fused<T, TX, TY, K, EPI><<<(unsigned)c->tiles.size(), Sh::THREADS, fused_smem_bytes<T, TX, TY, K>(), s>>>(
+    static unsigned grid = 0;  // per instantiation: the occupancy does not depend on the batch
+    if (!grid) grid = persistent_grid(k_fused<T, TX, TY, K, EPI>, Sh::THREADS, fused_smem_bytes<T, TX, TY, K>(), ~0ull);
+    const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
+    k_fused<T, TX, TY, K, EPI><<<g, Sh::THREADS, fused_smem_bytes<T, TX, TY, K>(), s>>>(
         c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first,
         (c->vec_ok && K % 2 == 0) ? 1 : 0, (const T*)c->field(buf, 0), (const T*)c->field(buf, 1), (const T*)c->field(buf, 2), (T*)c->field(buf ^ 1, 0),
         (T*)c->field(buf ^ 1, 1), (T*)c->field(buf ^ 1, 2), cin, cout, c->at<int64_t>(c->lay.fstep),
         c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum), c->at<uint32_t>(c->lay.intents),
-        c->at<uint32_t>(c->lay.icount), c->P);
+        c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr), (int)c->tiles.size(), pass, c->P);
 }
 
 template <int TX, int TY, int K, bool EPI>
 void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin,
-                     uint32_t* cout) {
+                     uint32_t* cout, int pass) {
     using Sh = FusedShape1<TX, TY, K>;
-    k_fused1<TX, TY, K, EPI><<<(unsigned)c->tiles.size(), Sh::THREADS, fused1_smem_bytes<TX, TY, K>(), s>>>(
+    static unsigned grid = 0;
+    if (!grid) grid = persistent_grid(k_fused1<TX, TY, K, EPI>, Sh::THREADS, fused1_smem_bytes<TX, TY, K>(), ~0ull);
+    const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
+    k_fused1<TX, TY, K, EPI><<<g, Sh::THREADS, fused1_smem_bytes<TX, TY, K>(), s>>>(
         c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first,
         (const float*)c->field(buf, 0), (const float*)c->field(buf, 1), (const float*)c->field(buf, 2),
         (float*)c->field(buf ^ 1, 0), (float*)c->field(buf ^ 1, 1), (float*)c->field(buf ^ 1, 2), cin, cout,
         c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
-        c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->P);
+        c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr),
+        (int)c->tiles.size(), pass, c->P);
 }
 
 template <typename T, int K, bool EPI>
-void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout) {
+void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
+                    int pass) {
     if constexpr (std::is_same<T, float>::value) {
-        if (c->shape == 3) return launch_fused1_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
-        if (c->shape == 4) return launch_fused1_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
+        if (c->shape == 3) return launch_fused1_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+        if (c->shape == 4) return launch_fused1_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     }
-    if (c->shape == 2) launch_fused_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
-    else launch_fused_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout);
+    if (c->shape == 2) launch_fused_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+    else launch_fused_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
 }
 
 // allow the dynamic shared memory of every fused instantiation of type T (done once, outside any capture)
@@ -326,13 +351,13 @@ cudaError_t fused_attrs() {
 
 template <typename T>
 void launch_fused(sim_ctx* c, cudaStream_t s, int k_off, int K, bool epi, int first, int buf, const uint32_t* cin,
-                  uint32_t* cout) {
+                  uint32_t* cout, int pass) {
     if (K == 1) {
-        if (epi) launch_fused_k<T, 1, true>(c, s, k_off, first, buf, cin, cout);
-        else launch_fused_k<T, 1, false>(c, s, k_off, first, buf, cin, cout);
+        if (epi) launch_fused_k<T, 1, true>(c, s, k_off, first, buf, cin, cout, pass);
+        else launch_fused_k<T, 1, false>(c, s, k_off, first, buf, cin, cout, pass);
     } else {
-        if (epi) launch_fused_k<T, 2, true>(c, s, k_off, first, buf, cin, cout);
-        else launch_fused_k<T, 2, false>(c, s, k_off, first, buf, cin, cout);
+        if (epi) launch_fused_k<T, 2, true>(c, s, k_off, first, buf, cin, cout, pass);
+        else launch_fused_k<T, 2, false>(c, s, k_off, first, buf, cin, cout, pass);
     }
 }
 
@@ -355,7 +380,7 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, in
             const bool epi = j == np - 1;
             if (epi && ev) cudaEventRecord(ev[1], s);
             uint32_t* cout = epi ? c->cells(start_cell ^ 1) : c->cells(start_cell);
-            launch_fused<T>(c, s, k_off, c->pass_k(j), epi, j == 0, buf, c->cells(start_cell), cout);
+            launch_fused<T>(c, s, k_off, c->pass_k(j), epi, j == 0, buf, c->cells(start_cell), cout, j);
             buf ^= 1;
         }
         if (ev) cudaEventRecord(ev[2], s);
@@ -366,7 +391,8 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, in
         if (ev) cudaEventRecord(ev[3], s);
         k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                           c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
-                                          c->at<unsigned long long>(c->lay.claim));
+                                          c->at<unsigned long long>(c->lay.claim), c->at<uint32_t>(c->lay.tile_ctr),
+                                          c->passes(), kMaxPasses);
         if (ev) cudaEventRecord(ev[4], s);
         return cuda_check(c, cudaGetLastError(), "step launch");
     }
@@ -392,7 +418,7 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, in
     if (ev) cudaEventRecord(ev[3], s);
     k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                       c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
-                                      c->at<unsigned long long>(c->lay.claim));
+                                      c->at<unsigned long long>(c->lay.claim), nullptr, 0, kMaxPasses);
     if (ev) cudaEventRecord(ev[4], s);
     return cuda_check(c, cudaGetLastError(), "step launch");
 }
@@ -520,6 +546,7 @@ sim_status set_shape(sim_ctx* c, int sh, const std::vector<int32_t>& L) {
     drop_graphs(c);
     cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
                                     cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.tile_ctr, 0, sizeof(uint32_t) * 2 * kMaxPasses, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     return cuda_check(c, e, "set shape");
 }
@@ -905,6 +932,7 @@ sim_status sim_set_clock(sim_ctx* c, int64_t step) {
     // stale claims carry step tags that could outrank the new clock: clear them with the work-list counters
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.claim, 0, 8 * (size_t)c->total_sites, c->stream);
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.icount, 0, 8, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.tile_ctr, 0, sizeof(uint32_t) * 2 * kMaxPasses, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_check(c, e, "set clock");
     c->clock = step;
@@ -1032,6 +1060,7 @@ sim_status sim_load_state(sim_ctx* c, const void* buf, size_t bytes) {
     if (!e) e = cudaMemcpyAsync(c->ws + c->lay.clock, &h.clock, sizeof h.clock, cudaMemcpyHostToDevice, c->stream);
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.claim, 0, 8 * (size_t)c->total_sites, c->stream);
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.icount, 0, 8, c->stream);
+    if (!e) e = cudaMemsetAsync(c->ws + c->lay.tile_ctr, 0, sizeof(uint32_t) * 2 * kMaxPasses, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_check(c, e, "load state");
     c->clock = h.clock;

@@ -109,6 +109,18 @@ template <>
 __device__ __forceinline__ float lds1<__half>(const __half* p) { return __half2float(*p); }
 
 constexpr int kDepth = 4;              // planes in flight per CTA
+constexpr int kMaxPasses = 32;         // tile-ticket slots per step parity (n_sub <= 64)
+
+// Persistent scheduling: each CTA takes tiles by atomic ticket from the slot
+// of this (step parity, pass); the division-resolve kernel of a step clears
+// the slots of the next one.  Tiles are sorted longest first.
+__device__ __forceinline__ int next_tile(uint32_t* ctr, int64_t step, int pass, int* s_tile) {
+    if (threadIdx.x == 0) *s_tile = (int)atomicAdd(ctr + (int)(step & 1) * kMaxPasses + pass, 1u);
+    __syncthreads();
+    const int t = *s_tile;
+    __syncthreads();  // every thread has read the ticket before thread 0 draws the next one
+    return t;
+}
 constexpr int kStages = kDepth + 2;    // a plane's stage is reused once its x/y neighbours were consumed
 
 // dynamic shared memory of a fused pass
@@ -125,7 +137,8 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
             int k_off, int first, int vec_ok, const T* __restrict__ iO, const T* __restrict__ iG,
             const T* __restrict__ iH, T* __restrict__ oO, T* __restrict__ oG, T* __restrict__ oH, const uint32_t* cin,
             uint32_t* cout, const int64_t* __restrict__ fstep, const double* __restrict__ fdose,
-            double* __restrict__ cum_dose, uint32_t* __restrict__ intents, uint32_t* __restrict__ icount, Params P) {
+            double* __restrict__ cum_dose, uint32_t* __restrict__ intents, uint32_t* __restrict__ icount,
+            uint32_t* __restrict__ tile_ctr, int n_tiles, int pass, Params P) {
     using S = FusedShape<TX, TY, K>;
     constexpr int HX = S::HX, HY = S::HY, NC = S::NC, PX = S::PX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,11 +147,15 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kStages * 3 * NC * sizeof(T));
     float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kStages * NC * (3 * sizeof(T) + sizeof(uint32_t)));
     __shared__ float s_dose;
+    __shared__ int s_tile;
 
-    const Tile tl = tiles[blockIdx.x];
-    const Proto pr = protos[tl.p];
     const int64_t step = *clock + k_off;
-    if (step >= pr.t_end) return;
+    for (;;) {
+    const int ti = next_tile(tile_ctr, step, pass, &s_tile);
+    if (ti >= n_tiles) break;
+    const Tile tl = tiles[ti];
+    const Proto pr = protos[tl.p];
+    if (step >= pr.t_end) continue;
     if (threadIdx.x == 0) {
         const double d = first ? dose_at(pr, fstep, fdose, step) : 0.0;
         s_dose = (float)d;
@@ -383,7 +400,9 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
         if (ib + 1 < n_it) iteration(std::integral_constant<int, 1>{}, zl0 + ib + 1);
         if (ib + 2 < n_it) iteration(std::integral_constant<int, 2>{}, zl0 + ib + 2);
     }
-    cp_async_wait<0>();  // no copy may still target this CTA's shared memory when it exits
+    cp_async_wait<0>();  // no copy may still target this CTA's shared memory after the tile
+    __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -409,7 +428,8 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
              int k_off, int first, const float* __restrict__ iO, const float* __restrict__ iG,
              const float* __restrict__ iH, float* __restrict__ oO, float* __restrict__ oG, float* __restrict__ oH,
              const uint32_t* cin, uint32_t* cout, const int64_t* __restrict__ fstep, const double* __restrict__ fdose,
-             double* __restrict__ cum_dose, uint32_t* __restrict__ intents, uint32_t* __restrict__ icount, Params P) {
+             double* __restrict__ cum_dose, uint32_t* __restrict__ intents, uint32_t* __restrict__ icount,
+             uint32_t* __restrict__ tile_ctr, int n_tiles, int pass, Params P) {
     using S = FusedShape1<TX, TY, K>;
     constexpr int HX = S::HX, HY = S::HY, NC = S::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -417,11 +437,15 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kStages * 3 * NC * sizeof(float));
     float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kStages * NC * 4 * sizeof(float));
     __shared__ float s_dose;
+    __shared__ int s_tile;
 
-    const Tile tl = tiles[blockIdx.x];
-    const Proto pr = protos[tl.p];
     const int64_t step = *clock + k_off;
-    if (step >= pr.t_end) return;
+    for (;;) {
+    const int ti = next_tile(tile_ctr, step, pass, &s_tile);
+    if (ti >= n_tiles) break;
+    const Tile tl = tiles[ti];
+    const Proto pr = protos[tl.p];
+    if (step >= pr.t_end) continue;
     if (threadIdx.x == 0) {
         const double d = first ? dose_at(pr, fstep, fdose, step) : 0.0;
         s_dose = (float)d;
@@ -575,6 +599,8 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
         if (ib + 2 < n_it) iteration(std::integral_constant<int, 2>{}, zl0 + ib + 2);
     }
     cp_async_wait<0>();
+    __syncthreads();
+    }
 }
 
 }  // namespace simdev

@@ -236,10 +236,14 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const Proto* __restrict__ 
                                                       uint32_t* __restrict__ cell, const uint32_t* __restrict__ intents,
                                                       uint32_t* __restrict__ icount,
                                                       const uint32_t* __restrict__ target,
-                                                      const unsigned long long* __restrict__ claim) {
+                                                      const unsigned long long* __restrict__ claim,
+                                                      uint32_t* __restrict__ tile_ctr, int n_pass, int slots) {
     const int64_t step = *clock + k_off;
     const uint32_t n = icount[step & 1];
     if (blockIdx.x == 0 && threadIdx.x == 0) icount[(step + 1) & 1] = 0;
+    // tile tickets of the next step's fused passes (slots per step parity)
+    if (tile_ctr && blockIdx.x == 0 && (int)threadIdx.x < n_pass)
+        tile_ctr[(int)((step + 1) & 1) * slots + threadIdx.x] = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t t = target[i];
         if (t == 0xffffffffu) continue;

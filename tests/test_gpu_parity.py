@@ -293,3 +293,30 @@ def test_full_size_batch_in_bench_configuration(cuda, orc):
         for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
             assert np.max(np.abs(g - o)) / m < 1e-4
         assert np.array_equal(sim.counts()[p][:2], ref["counts"][:2])
+
+
+def test_ragged_batch_persistent_fused_equals_substep_and_oracle(cuda, orc):
+    """Ragged batch (lattices 16..64 from radii 3..12, 2-8 hypofractionated
+    fractions): the persistent fused path equals the substep path bit for bit
+    over two simulated hours, and sampled protocols equal the oracle."""
+    from paper_2303_08123_b300 import csr
+    from synth import workloads
+    L, R, prot = workloads.ragged_batch(40, seed=9, r_min=3, r_max=12, f_min=2, f_max=8)
+    prot = [(d, [0.5] + w[1:]) for d, w in prot]  # a fraction within the first hour
+    out = []
+    for kw in (dict(path="substep"), dict(path="fused")):
+        sim = _sim(L, R, hours=2, t_end_steps=1200, **kw)
+        sim.load_protocols(*csr(prot))
+        if kw["path"] == "fused":
+            sim.autotune(2)
+        sim.run(0)
+        out.append(([sim.get_state(p)[3] for p in range(len(L))], sim.counts(), sim.field_totals()[0]))
+        sim.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+    for p in (0, 17, 39):
+        ref = orc.run(P0, int(L[p]), int(R[p]), SEED, p, prot[p][0], prot[p][1], t_end_steps=1200, hours=2)
+        assert np.array_equal(out[1][0][p], ref["state"].cell), p
+        assert np.array_equal(out[1][1][p], ref["counts"])
