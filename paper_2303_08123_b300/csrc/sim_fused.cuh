@@ -416,10 +416,12 @@ struct FusedShape1 {
     static constexpr int THREADS = (NC + 31) / 32 * 32;
 };
 
+constexpr int kStages1 = 8;  // stages of the one-column kernel (a power of two >= kDepth + 2)
+
 template <int TX, int TY, int K>
 constexpr size_t fused1_smem_bytes() {
     using S = FusedShape1<TX, TY, K>;
-    return (size_t)kStages * S::NC * 4 * sizeof(float) + (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::NC * sizeof(float);
+    return (size_t)kStages1 * S::NC * 4 * sizeof(float) + (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::NC * sizeof(float);
 }
 
 template <int TX, int TY, int K, bool EPI>
@@ -432,14 +434,30 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
              uint32_t* __restrict__ tile_ctr, int n_tiles, int pass, Params P) {
     using S = FusedShape1<TX, TY, K>;
     constexpr int HX = S::HX, HY = S::HY, NC = S::NC;
+    constexpr int kS1 = kStages1;  // power of two: stage index = (plane - zl0) & (kS1 - 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* stage_f = reinterpret_cast<float*>(smem_raw);
-    uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kStages * 3 * NC * sizeof(float));
-    float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kStages * NC * 4 * sizeof(float));
+    uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * 3 * NC * sizeof(float));
+    float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float));
     __shared__ float s_dose;
     __shared__ int s_tile;
 
+    const int tid = threadIdx.x;
+    const bool act = tid < NC;
+    const int cx = tid % HX, cy = tid / HX;
+    // per-thread constants of the tile-independent geometry
+    bool inreg[K + 1];
+#pragma unroll
+    for (int l = 1; l <= K; ++l) inreg[l] = act && cx >= l && cx < HX - l && cy >= l && cy < HY - l;
+    const bool outtile = act && cx >= K && cx < K + TX && cy >= K && cy < K + TY;
+    float* const my_stage = stage_f + tid;     // + s * 3 * NC + f * NC
+    uint32_t* const my_cell = stage_c + tid;   // + s * NC
+    float* const my_lv = slv + tid;            // + ((l - 1) * 2 + parity) * 3 * NC + f * NC
+    const uint32_t lane = threadIdx.x & 31u;
+    const bool diffuse = (P.flags & kFDiffusion) != 0, react = (P.flags & kFReaction) != 0;
+
     const int64_t step = *clock + k_off;
+    uint32_t* cnt = icount + (step & 1);
     for (;;) {
     const int ti = next_tile(tile_ctr, step, pass, &s_tile);
     if (ti >= n_tiles) break;
@@ -453,30 +471,28 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
     }
     const int L = pr.L;
     const int LL = L * L;
-    const int tid = threadIdx.x;
-    const bool act = tid < NC;
-    const int cx = tid % HX, cy = tid / HX;
     const int x = tl.x0 - K + cx, y = tl.y0 - K + cy;
     const bool in = act && x >= 0 && x < L && y >= 0 && y < L;
     const bool fxy = !in || x == 0 || y == 0 || x == L - 1 || y == L - 1;
-    const bool outc = in && cx >= K && cx < K + TX && cy >= K && cy < K + TY;
+    const bool outc = outtile && in;
     const int col = in ? x + L * y : 0;
     const int z0 = tl.z0, z1 = tl.z1;
     const int zl0 = max(0, z0 - K), zl1 = min(L - 1, z1 - 1 + K);
-    const bool diffuse = (P.flags & kFDiffusion) != 0, react = (P.flags & kFReaction) != 0;
-    const uint32_t lane = threadIdx.x & 31u;
-    uint32_t* cnt = icount + (step & 1);
-    const float* gf[3] = {iO + pr.site0 + col, iG + pr.site0 + col, iH + pr.site0 + col};
+    const float* g0 = iO + pr.site0 + col;
+    const float* g1 = iG + pr.site0 + col;
+    const float* g2 = iH + pr.site0 + col;
     const uint32_t* gC = cin + pr.site0 + col;
+    const bool fetch = act;  // every active thread copies (zero-filled outside the lattice)
 
     auto prefetch = [&](int j) {
-        if (act && j <= zl1) {
-            const int s = (j - zl0) % kStages;
+        if (fetch && j <= zl1) {
+            const int s = (j - zl0) & (kS1 - 1);
             const int o = j * LL;
-            float* sf = stage_f + (size_t)s * 3 * NC + tid;
-#pragma unroll
-            for (int f = 0; f < 3; ++f) cp_async(sf + f * NC, gf[f] + o, 4, in);
-            cp_async(stage_c + (size_t)s * NC + tid, gC + o, 4, in);
+            float* sf = my_stage + s * 3 * NC;
+            cp_async(sf, g0 + o, 4, in);
+            cp_async(sf + NC, g1 + o, 4, in);
+            cp_async(sf + 2 * NC, g2 + o, 4, in);
+            cp_async(my_cell + s * NC, gC + o, 4, in);
         }
         cp_async_commit();
     };
@@ -502,13 +518,15 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
         __syncthreads();
         prefetch(i + kDepth);
         const bool loaded = i <= zl1;
-        const int st = (i - zl0) % kStages;
+        const int st = (i - zl0) & (kS1 - 1);
         float v0[3] = {0.f, 0.f, 0.f};
         uint32_t w = 0;
         if (loaded && act) {
-#pragma unroll
-            for (int f = 0; f < 3; ++f) v0[f] = stage_f[(size_t)st * 3 * NC + f * NC + tid];
-            w = stage_c[(size_t)st * NC + tid];
+            const float* sf = my_stage + st * 3 * NC;
+            v0[0] = sf[0];
+            v0[1] = sf[NC];
+            v0[2] = sf[2 * NC];
+            w = my_cell[st * NC];
         }
         if (dose > 0.f && loaded && !fxy && i > 0 && i < L - 1 && (w & kKindMask) != kEmpty) {
             const float Sv = lq_survival(w & kKindMask, v0[0], dose, P);
@@ -530,25 +548,23 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
             const int sq = (ph - l + 6) % 3, sm = (ph - l - 1 + 6) % 3, sp = (ph - l + 1 + 6) % 3;
             const int lo = (zl0 == 0) ? 0 : zl0 + l;
             const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
-            const bool reg = act && cx >= l && cx < HX - l && cy >= l && cy < HY - l && q >= lo && q <= hi;
+            const bool reg = inreg[l] && q >= lo && q <= hi;
             float v[3] = {0.f, 0.f, 0.f};
             if (reg) {
                 if (fxy || q == 0 || q == L - 1) {
 #pragma unroll
                     for (int f = 0; f < 3; ++f) v[f] = ring[l - 1][f][sq];
                 } else {
+                    // level l-1 plane q: the stage of plane q (l = 1) or the shared plane of level l-1
+                    const float* pl = (l == 1) ? my_stage + ((q - zl0) & (kS1 - 1)) * 3 * NC
+                                               : my_lv + ((l >= 2 ? l - 2 : 0) * 2 + (q & 1)) * 3 * NC;
 #pragma unroll
                     for (int f = 0; f < 3; ++f) {
                         const float c = ring[l - 1][f][sq];
-                        float t = c;
-                        if (diffuse) {
-                            const float* pf = (l == 1)
-                                ? stage_f + (size_t)((q - zl0) % kStages) * 3 * NC + f * NC + tid
-                                : slv + ((size_t)((l >= 2) ? l - 2 : 0) * 2 + (q & 1)) * 3 * NC + f * NC + tid;
-                            t = stencil_t(c, pf[-1], pf[1], pf[-HX], pf[HX], ring[l - 1][f][sm], ring[l - 1][f][sp],
-                                          P.lam[f]);
-                        }
-                        v[f] = t;
+                        const float* pf = pl + f * NC;
+                        v[f] = diffuse ? stencil_t(c, pf[-1], pf[1], pf[-HX], pf[HX], ring[l - 1][f][sm],
+                                                   ring[l - 1][f][sp], P.lam[f])
+                                       : c;
                     }
                     float uO = 0.f, uG = 0.f, pHv = 0.f;
                     const uint32_t kq = wr[sq] & kKindMask;
@@ -559,10 +575,11 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS)
                 }
             }
             if (l < K) {
+                float* dst = my_lv + ((l - 1) * 2 + (q & 1)) * 3 * NC;
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
                     ring[l][f][sq] = v[f];
-                    if (act) slv[((size_t)(l - 1) * 2 + (q & 1)) * 3 * NC + f * NC + tid] = v[f];
+                    if (act) dst[f * NC] = v[f];
                 }
             } else {
                 bool want = false;
