@@ -66,6 +66,13 @@ int mlp_set_params(mlp_ctx* ctx, const float* host);
 int mlp_gemm_bf16(const void* d_A, const void* d_B, float* d_C, int M, int N, int K, uint32_t* d_status,
                   void* cuda_stream);
 
+/* Failure-path probe (no counterpart in the paper): one CTA waits on an
+ * mbarrier that nothing arrives at, polling at most spin_limit times (1 ..
+ * 2^26), and then writes 1 to *d_status (device u32) exactly as a timed-out
+ * GEMM wait would.  Lets callers and tests check that a device-side timeout is
+ * reported and leaves the context usable.  Asynchronous. */
+int mlp_wait_probe(uint32_t spin_limit, uint32_t* d_status, void* cuda_stream);
+
 void mlp_destroy(mlp_ctx* ctx);
 
 #ifdef __cplusplus

@@ -420,6 +420,12 @@ int mlp_gemm_bf16(const void* d_A, const void* d_B, float* d_C, int M, int N, in
     return gemm(d_A, d_B, d_C, M, N, K, d_status, (cudaStream_t)stream);
 }
 
+int mlp_wait_probe(uint32_t spin_limit, uint32_t* d_status, void* stream) {
+    if (!d_status || spin_limit == 0 || spin_limit > (1u << 26)) return -1;
+    tcg::k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(spin_limit, d_status);
+    return cuda_status(cudaGetLastError());
+}
+
 void mlp_destroy(mlp_ctx* c) { delete c; }
 
 }  // extern "C"

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sim.h"
 #include "sim_kernels.cuh"
 #include "sim_fused.cuh"
@@ -740,9 +742,16 @@ sim_status sim_reset(sim_ctx* c) {
     return reset_device(c);
 }
 
+// NVTX range for the duration of a host call (visible in Nsight timelines)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 sim_status sim_run(sim_ctx* c, int64_t max_steps) {
     if (!c) return SIM_EINVAL;
     if (!c->loaded) return fail(c, SIM_ESTATE, "load protocols before running");
+    NvtxRange nvtx("sim_run");
     int64_t target = max_t_end(c);
     if (max_steps > 0 && c->clock + max_steps < target) target = c->clock + max_steps;
     const bool graphs = c->cfg.use_graphs != 0;
@@ -808,6 +817,7 @@ sim_status sim_profile_steps(sim_ctx* c, int n_steps, double* ms, int64_t* launc
 
 sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     if (!c || n_steps < 1) return SIM_EINVAL;
+    NvtxRange nvtx("sim_autotune");
     if (!c->loaded) return fail(c, SIM_ESTATE, "load protocols before autotuning");
     for (int k = 0; k < kNumShapes; ++k)
         if (ms) ms[k] = -1.0;

@@ -57,10 +57,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// wait for the phase with the given parity to complete; false after kSpinLimit polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// wait for the phase with the given parity to complete; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done = 0;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -190,6 +190,18 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __r
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// Failure-path probe: waits on an mbarrier that nothing will ever arrive at,
+// with `limit` polls, and reports the timeout through *status exactly as the
+// GEMM does.  Lets a test exercise the error path without hanging the GPU.
+__global__ void k_wait_probe(uint32_t limit, uint32_t* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait(&bar, 0, limit)) atomicExch(status, 1u);
+    }
 }
 
 }  // namespace tcg

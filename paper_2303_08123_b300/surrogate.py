@@ -24,6 +24,7 @@ SIGNATURES = {
     "mlp_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "mlp_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float)]),
     "mlp_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "mlp_wait_probe": (ctypes.c_int, [ctypes.c_uint32, _vp, _vp]),
     "mlp_destroy": (None, [_vp]),
 }
 

@@ -69,3 +69,16 @@ def test_training_reduces_loss(cuda):
     Xv, tv = _data(rng, 512)
     pred = net.predict(Xv)
     assert np.corrcoef(pred, tv)[0, 1] > 0.95
+
+
+def test_bounded_wait_times_out_into_a_status_and_the_context_stays_usable(cuda):
+    torch = cuda
+    from paper_2303_08123_b300.surrogate import gemm_bf16, load_library
+    lib = load_library()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.mlp_wait_probe(1000, st.data_ptr(), torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 1  # the wait ran out and said so
+    A = torch.ones(128, 32, dtype=torch.bfloat16, device="cuda")
+    C = gemm_bf16(A, A[:16])  # the device still works afterwards
+    assert float(C[0, 0]) == 32.0
