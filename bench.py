@@ -233,9 +233,12 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sim = Simulator(Ls, Rs, seed=SEED, precision=args.precision, hours=hours,
-                    dose_cap_gy=30.0, device=dev, path=args.path)
+                    dose_cap_gy=30.0, device=dev, path=args.path, tile_shape=args.tile_shape)
     sim.load_protocols(off, d, w)
-    shape, shape_ms = sim.autotune(10) if args.path == "fused" else (0, None)  # re-seeds the batch at step 0
+    if args.path == "fused" and args.tile_shape == 0:
+        shape, shape_ms = sim.autotune(10)  # re-seeds the batch at step 0
+    else:
+        shape, shape_ms = args.tile_shape, None
     stream = torch.cuda.current_stream(dev)
     for _ in range(W):
         sim.run(STEPS_PER_HOUR)
@@ -265,7 +268,7 @@ def run_ours(args):
     interior = float(np.sum((Ls.astype(np.float64) - 2) ** 3))
     es = 4 if args.precision == "fp32" else 2
     if args.path == "fused":
-        kn = "k_fused1" if shape in (3, 4) else "k_fused"
+        kn = "k_fused1" if shape in (3, 4) else "k_fused"  # shape 0 only on the substep path
         classes = {f"{kn} (first pass: irradiation + 2 substeps)": (kms[0], kl[0], interior * (6 * es + 4)),
                    f"{kn} (last pass: 2 substeps + cell update)": (kms[1], kl[1], interior * (6 * es + 8))}
         traffic_key = {f"{kn} (first pass: irradiation + 2 substeps)": f"{kn}_first_shape{shape}",
@@ -352,6 +355,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "substep"])
+    ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-4 (0: autotune)")
     ap.add_argument("--workload", default="ga_batch", choices=["ga_batch", "ragged"],
                     help="ga_batch: 256 x 64^3 (default); ragged: 1,024 protocols on 32^3-112^3")
     ap.add_argument("--protocols", type=int, default=256, help="batch size per GPU (smaller: profiling cases)")
