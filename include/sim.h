@@ -163,6 +163,13 @@ sim_status sim_get_state(sim_ctx* ctx, int p, float* O, float* G, float* H, uint
 sim_status sim_set_state(sim_ctx* ctx, int p, const float* O, const float* G, const float* H,
                          const uint32_t* cell);
 
+/* Copy protocol slot ps of context src (fields and cell words) into slot pd
+ * of context dst on the device.  Both slots must have the same lattice side
+ * and both contexts the same storage precision; src must not be running work
+ * that changes that slot (the copy is ordered on dst's stream only).  Used to
+ * start many evaluations from one grown tumour (a tumour case library). */
+sim_status sim_copy_lattice(sim_ctx* dst, int pd, const sim_ctx* src, int ps);
+
 /* Checkpoint the whole batch (fields, cells, clock, delivered dose, counts)
  * into a host buffer; with buf == NULL only *bytes is set to the size needed.
  * Philox is counter-based, so a restored run continues bit for bit.

@@ -975,6 +975,25 @@ sim_status sim_get_state(sim_ctx* c, int p, float* O, float* G, float* H, uint32
     return read_status(c);
 }
 
+sim_status sim_copy_lattice(sim_ctx* dst, int pd, const sim_ctx* src, int ps) {
+    if (!dst || !src || pd < 0 || pd >= dst->n || ps < 0 || ps >= src->n) return SIM_EINVAL;
+    const Proto& a = dst->proto[pd];
+    const Proto& b = src->proto[ps];
+    if (a.L != b.L || dst->cfg.precision != src->cfg.precision)
+        return fail(dst, SIM_EINVAL, "lattice side or precision differ");
+    const int64_t n = (int64_t)a.L * a.L * a.L;
+    const size_t es = elem_size(dst->cfg.precision);
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 3 && !e; ++f)
+        for (int k = 0; k < 2 && !e; ++k)  // both buffers: faces are read from either
+            e = cudaMemcpyAsync((char*)dst->field(k, f) + a.site0 * es, (const char*)src->field(src->cur, f) + b.site0 * es,
+                                n * es, cudaMemcpyDeviceToDevice, dst->stream);
+    if (!e)
+        e = cudaMemcpyAsync(dst->cells(dst->ccur) + a.site0, src->cells(src->ccur) + b.site0, 4 * n,
+                            cudaMemcpyDeviceToDevice, dst->stream);
+    return cuda_check(dst, e, "copy lattice");
+}
+
 sim_status sim_set_state(sim_ctx* c, int p, const float* O, const float* G, const float* H, const uint32_t* cell) {
     if (!c || p < 0 || p >= c->n) return SIM_EINVAL;
     const Proto& pr = c->proto[p];

@@ -86,6 +86,7 @@ SIGNATURES = {
     "sim_set_clock": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "sim_get_state": (ctypes.c_int, [_vp, ctypes.c_int, _f32p, _f32p, _f32p, _u32p]),
     "sim_set_state": (ctypes.c_int, [_vp, ctypes.c_int, _f32p, _f32p, _f32p, _u32p]),
+    "sim_copy_lattice": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int]),
     "sim_save_state": (ctypes.c_int, [_vp, _vp, _P(ctypes.c_size_t)]),
     "sim_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "sim_profile_steps": (ctypes.c_int, [_vp, ctypes.c_int, _f64p, _i64p]),
@@ -268,6 +269,10 @@ class Simulator:
         ms = np.full(4, -1.0)
         self._call("sim_autotune", int(n_steps), ctypes.byref(best), _ptr(ms, ctypes.c_double))
         return best.value, ms
+
+    def copy_lattice(self, p: int, src: "Simulator", q: int):
+        """Slot p of this batch <- slot q of `src` (device to device)."""
+        self._call("sim_copy_lattice", p, src._ctx, q)
 
     def save_state(self) -> bytes:
         size = ctypes.c_size_t(0)
