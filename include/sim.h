@@ -57,6 +57,12 @@ typedef struct {
     double alpha, beta, omf_m, omf_K;     /* LQ survival and oxygen modification */
     double phi[5];        /* radiosensitivity factors G1, S, G2, M, quiescent */
     double O_q, G_q, pH_q, G_d, pH_d;     /* quiescence and death thresholds */
+    double repair_half_h; /* sublethal-damage repair half-time in hours.  0: repair is complete
+                             between fractions (each fraction an independent LQ kill).  > 0:
+                             incomplete repair -- a fraction of dose D at time t is scored with
+                             -ln S = a D + b D (D + 2 H), H = sum over earlier fractions of
+                             D_i 2^(-(t - t_i) / repair_half_h), the interaction term of the
+                             LQ model extended to incompletely repaired damage (Thames 1985) */
 } sim_params;
 
 typedef struct {
@@ -120,6 +126,26 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
  */
 sim_status sim_load_protocols(sim_ctx* ctx, int n, const int32_t* offsets, const double* dose_gy,
                               const double* wait_h);
+
+/*
+ * Load one protocol per slot from dose vectors already on the device ("Protocol
+ * Representation"): d_units (device, n x n_slots bytes, row p = slot p) holds
+ * in entry i the dose given i * 30 min after the start (step 300 i), in units
+ * of unit_gy; 0 = no fraction.  Resets every slot to its seeded spheroid at
+ * step 0 like sim_load_protocols.  Needs a fixed horizon (t_end_steps > 0):
+ * the host never learns the protocols.  A row with more than max_fractions
+ * fractions or a total above dose_cap_gy runs without fractions and the next
+ * synchronising call returns SIM_EINVAL.  With repair_half_h > 0 the
+ * quadratic partners of the fractions are computed on the device.
+ * Asynchronous (the caller keeps d_units unchanged until the stream passes
+ * this call).  Errors: SIM_EINVAL (arguments), SIM_ESTATE (no fixed horizon).
+ */
+sim_status sim_load_dose_vectors(sim_ctx* ctx, const uint8_t* d_units, int n_slots, double unit_gy);
+
+/* Final live count (device i32, n entries, may be NULL) and fitness
+ * n_max - n (device FP32, n entries, may be NULL) of every protocol, written
+ * on the stream without synchronising (the device-resident GA reads them). */
+sim_status sim_fitness_device(sim_ctx* ctx, int32_t* d_count, float* d_fitness);
 
 /* Re-seed every spheroid and set the clock to step 0 (asynchronous). */
 sim_status sim_reset(sim_ctx* ctx);

@@ -57,7 +57,8 @@ class _Params(ctypes.Structure):
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("omf_m", ctypes.c_double),
         ("omf_K", ctypes.c_double), ("phi", ctypes.c_double * 5),
         ("O_q", ctypes.c_double), ("G_q", ctypes.c_double), ("pH_q", ctypes.c_double),
-        ("G_d", ctypes.c_double), ("pH_d", ctypes.c_double), ("near_tol", ctypes.c_double),
+        ("G_d", ctypes.c_double), ("pH_d", ctypes.c_double), ("repair_half_h", ctypes.c_double),
+        ("near_tol", ctypes.c_double),
     ]
 
 
@@ -77,7 +78,7 @@ def _pack(p: Params, near_tol: float = NEAR_TOL) -> _Params:
     for i in range(3):
         s.lam[i] = p.lam[i]
     for n in ("medium_O", "medium_G", "medium_pH", "q_O", "K_O", "q_G", "K_G", "k_an", "O_an", "q_H", "f_Q",
-              "alpha", "beta", "omf_m", "omf_K", "O_q", "G_q", "pH_q", "G_d", "pH_d"):
+              "alpha", "beta", "omf_m", "omf_K", "O_q", "G_q", "pH_q", "G_d", "pH_d", "repair_half_h"):
         setattr(s, n, float(getattr(p, n)))
     for i in range(5):
         s.phi[i] = p.phi[i]
@@ -102,7 +103,7 @@ def lib():
                               f64p, f64p, f64p, u32p]
         L.or_step.restype = ctypes.c_int
         L.or_step.argtypes = [P(_Params), ctypes.c_int, ctypes.c_int, u32p, ctypes.c_uint32, ctypes.c_uint32,
-                              ctypes.c_double, f64p, f64p, f64p, u32p, u8p, P(_Stats)]
+                              ctypes.c_double, ctypes.c_double, f64p, f64p, f64p, u32p, u8p, P(_Stats)]
         L.or_fraction_step.restype = ctypes.c_int64
         L.or_fraction_step.argtypes = [f64p, ctypes.c_int]
         L.or_run.restype = ctypes.c_int64
@@ -166,12 +167,14 @@ def init(p: Params, L: int, R: int, seed: int, init_word: int = 0xFFFFFFFF, bc: 
 
 
 def step(p: Params, st: State, seed: int, protocol: int, step_idx: int, dose: float = 0.0,
-         bc: int = BC_DIRICHLET, near_tol: float = NEAR_TOL):
-    """Advance `st` in place by one CA step; returns (near flags per site, stats dict)."""
+         bc: int = BC_DIRICHLET, near_tol: float = NEAR_TOL, unrepaired: float = 0.0):
+    """Advance `st` in place by one CA step; returns (near flags per site, stats dict).
+    `unrepaired`: dose of earlier fractions not yet repaired (incomplete-repair LQ term)."""
     pk = _pack(p, near_tol)
     near = np.zeros(st.L ** 3, dtype=np.uint8)
     stats = _Stats()
     lib().or_step(ctypes.byref(pk), st.L, bc, _ptr(_key(seed), ctypes.c_uint32), protocol, step_idx, float(dose),
+                  float(unrepaired),
                   _ptr(st.O, ctypes.c_double), _ptr(st.G, ctypes.c_double), _ptr(st.H, ctypes.c_double),
                   _ptr(st.cell, ctypes.c_uint32), _ptr(near, ctypes.c_uint8), ctypes.byref(stats))
     return near, stats.as_dict()

@@ -114,10 +114,13 @@ int64_t or_init(const or_params* P, int L, int R, int bc, const uint32_t key[2],
 /* ------------------------------------------------------------------ */
 /* Step 1: irradiation.  Survival of a cell of phase k at oxygen O under dose D
  * is the linear-quadratic S = exp(-a D - b D^2) with a = alpha*phi_k*OMF(O) and
- * b = beta*(phi_k*OMF(O))^2, OMF(O) = (m O + K) / (m (O + K)).  A cell whose
- * Philox uniform u satisfies u >= S is lethally hit (DOOMED). */
+ * b = beta*(phi_k*OMF(O))^2, OMF(O) = (m O + K) / (m (O + K)).  With incomplete
+ * repair between fractions the quadratic term also pairs D with the unrepaired
+ * dose Hu of earlier fractions: -ln S = a D + b (D^2 + 2 D Hu) (Thames 1985).  A
+ * cell whose Philox uniform u satisfies u >= S is lethally hit (DOOMED). */
 static void irradiate(const or_params* P, int L, const uint32_t key[2], uint32_t protocol, uint32_t step,
-                      double dose, const double* O, uint32_t* cell, uint8_t* near, or_stats* st) {
+                      double dose, double unrepaired, const double* O, uint32_t* cell, uint8_t* near,
+                      or_stats* st) {
     const int64_t N = (int64_t)L * L * L;
     for (int64_t s = 0; s < N; ++s) {
         uint32_t w = cell[s];
@@ -127,7 +130,7 @@ static void irradiate(const or_params* P, int L, const uint32_t key[2], uint32_t
         double mod = P->phi[kind - 1] * omf;
         double a = P->alpha * mod;
         double b = P->beta * mod * mod;
-        double S = exp(-a * dose - b * dose * dose);
+        double S = exp(-a * dose - b * (dose * dose + 2.0 * dose * unrepaired));
         uint32_t ctr[4] = {(uint32_t)s, step, (uint32_t)OR_PURPOSE_IRR, protocol};
         uint32_t r[4];
         or_philox4x32_10(ctr, key, r);
@@ -335,13 +338,14 @@ static void divide(const or_params* P, int L, int bc, const uint32_t key[2], uin
 }
 
 int or_step(const or_params* P, int L, int bc, const uint32_t key[2], uint32_t protocol, uint32_t step,
-            double dose, double* O, double* G, double* H, uint32_t* cell, uint8_t* near, or_stats* st_out) {
+            double dose, double unrepaired, double* O, double* G, double* H, uint32_t* cell, uint8_t* near,
+            or_stats* st_out) {
     const int64_t N = (int64_t)L * L * L;
     or_stats st;
     memset(&st, 0, sizeof st);
     if (near) memset(near, 0, (size_t)N);
 
-    if (dose > 0.0) irradiate(P, L, key, protocol, step, dose, O, cell, near, &st);
+    if (dose > 0.0) irradiate(P, L, key, protocol, step, dose, unrepaired, O, cell, near, &st);
 
     double* bufA[3] = {O, G, H};
     double* tmp = (double*)malloc(sizeof(double) * 3 * (size_t)N);
@@ -409,12 +413,16 @@ static int64_t run_impl(const or_params* P, int L, int R, const uint32_t key[2],
     double cum = 0.0;
     for (int64_t s = 0; s < T; ++s) {
         if (counts && s % 600 == 0 && s / 600 <= hours) counts[s / 600] = (int32_t)live;
-        double dose = 0.0;
-        for (int j = 0; j < n_frac; ++j)
+        double dose = 0.0, unrepaired = 0.0;
+        for (int j = 0; j < n_frac; ++j) {
             if (fstep[j] == s) dose += dose_gy[j];
+            /* earlier fractions, decayed with the repair half-time (none left if repair is complete) */
+            if (fstep[j] < s && P->repair_half_h > 0.0)
+                unrepaired += dose_gy[j] * pow(2.0, -(double)(s - fstep[j]) / 600.0 / P->repair_half_h);
+        }
         cum += dose;
         or_stats st;
-        or_step(P, L, OR_BC_DIRICHLET, key, protocol, (uint32_t)s, dose, O, G, H, cell, NULL, &st);
+        or_step(P, L, OR_BC_DIRICHLET, key, protocol, (uint32_t)s, dose, unrepaired, O, G, H, cell, NULL, &st);
         add_stats(&tot, &st);
         live = st.n_live;
     }

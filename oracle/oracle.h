@@ -36,6 +36,7 @@ typedef struct {
     double alpha, beta, omf_m, omf_K;
     double phi[5];        /* G1, S, G2, M, Q */
     double O_q, G_q, pH_q, G_d, pH_d;
+    double repair_half_h; /* sublethal-damage repair half-time (h); 0: complete repair */
     double near_tol;      /* relative tolerance that defines near-threshold */
 } or_params;
 
@@ -59,10 +60,12 @@ int64_t or_init(const or_params* P, int L, int R, int bc, const uint32_t key[2],
                 uint32_t init_word, double* O, double* G, double* H, uint32_t* cell);
 
 /* One CA step (irradiate if dose > 0, n_sub diffusion substeps, cell update,
- * division).  near (nullable) receives OR_NEAR_* bits per site.  Returns 0. */
+ * division).  unrepaired: dose of earlier fractions still unrepaired at this
+ * step (the H of the incomplete-repair LQ term; 0 with complete repair).
+ * near (nullable) receives OR_NEAR_* bits per site.  Returns 0. */
 int or_step(const or_params* P, int L, int bc, const uint32_t key[2], uint32_t protocol,
-            uint32_t step, double dose, double* O, double* G, double* H, uint32_t* cell,
-            uint8_t* near, or_stats* st);
+            uint32_t step, double dose, double unrepaired, double* O, double* G, double* H,
+            uint32_t* cell, uint8_t* near, or_stats* st);
 
 /* Fraction schedule: step of fraction j = round(600 * sum_{i<=j} wait_i). */
 int64_t or_fraction_step(const double* wait_h, int j);

@@ -22,6 +22,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 TARGETS = {
     "libsim.so": ["sim_api.cu"],
     "libmlp.so": ["mlp_api.cu"],
+    "libga.so": ["ga_api.cu"],
 }
 
 

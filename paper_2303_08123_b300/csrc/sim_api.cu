@@ -51,7 +51,7 @@ Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nb
     l.blocks = take(sizeof(Block) * nblocks);
     l.tiles = take(sizeof(Tile) * (ntiles > 0 ? ntiles : 1));
     l.fstep = take(sizeof(int64_t) * (nf > 0 ? nf : 1));
-    l.fdose = take(sizeof(double) * (nf > 0 ? nf : 1));
+    l.fdose = take(sizeof(double) * 2 * (nf > 0 ? nf : 1));  // doses, then their quadratic partners
     for (int b = 0; b < 2; ++b)
         for (int f = 0; f < 3; ++f) l.field[b][f] = take(es * total_sites);
     l.cell[0] = take(4 * total_sites);
@@ -88,6 +88,8 @@ bool valid_config(const sim_config* cfg, std::string* why) {
             return *why = "diffusion numbers must lie in [0, 1/6] (FTCS stability in 3-D)", false;
     if (cfg->hours < 0 || cfg->hours > 1000000) return *why = "hours out of range", false;
     if (cfg->max_fractions < 0 || cfg->max_fractions > 100000) return *why = "max_fractions out of range", false;
+    if (!std::isfinite(cfg->params.repair_half_h) || cfg->params.repair_half_h < 0.0)
+        return *why = "repair_half_h must be finite and >= 0", false;
     if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
     if (cfg->path < SIM_PATH_FUSED || cfg->path > SIM_PATH_SUBSTEP) return *why = "unknown kernel path", false;
     if (cfg->tile_shape < 0 || cfg->tile_shape > 4) return *why = "tile_shape must be in 0..4", false;
@@ -119,14 +121,17 @@ int pick_shape(const sim_config& cfg, int n, const int32_t* L) {
     return pick;
 }
 
-// Fused work list: column tiles of every protocol, split in z when the batch
-// has too few columns to fill the GPU.
-std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int shape) {
+// Fused work list: column tiles of every protocol still running (live[p] != 0;
+// live == nullptr: all), split in z when those have too few columns to fill the GPU.
+std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int shape,
+                             const uint8_t* live = nullptr) {
     const int TX = kTileShapes[shape][0], TY = kTileShapes[shape][1];
     int64_t cols = 0;
-    for (int p = 0; p < n; ++p) cols += (int64_t)((L[p] + TX - 1) / TX) * ((L[p] + TY - 1) / TY);
+    for (int p = 0; p < n; ++p)
+        if (!live || live[p]) cols += (int64_t)((L[p] + TX - 1) / TX) * ((L[p] + TY - 1) / TY);
     std::vector<Tile> t;
     for (int p = 0; p < n; ++p) {
+        if (live && !live[p]) continue;
         int zc = L[p];
         if (cfg.z_chunk > 0) zc = cfg.z_chunk;
         else if (cols < kTargetCtas) {
@@ -160,6 +165,7 @@ struct sim_ctx {
     std::vector<Proto> proto;
     std::vector<Block> blocks;
     std::vector<Tile> tiles;
+    std::vector<uint8_t> tile_live;  // protocols the fused work list covers
     int shape = 1;
     int vec_ok = 1;  // every lattice side even: column pairs start on even elements
     int64_t total_sites = 0;
@@ -506,6 +512,10 @@ sim_status read_status(sim_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(&st, c->ws + c->lay.status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_check(c, e, "synchronise");
+    if (st & kStatusBadProtocol)
+        return fail(c, SIM_EINVAL,
+                    "a protocol loaded from device dose vectors exceeds max_fractions or the dose cap "
+                    "(it was run without fractions)");
     if (st) return fail(c, SIM_ETIMEOUT, "device reported status " + std::to_string(st));
     return SIM_OK;
 }
@@ -544,13 +554,28 @@ void launch_totals(sim_ctx* c) {
 // Switch the fused work list to tile shape `sh` (rebuilds and uploads the tiles; drops captured graphs).
 sim_status set_shape(sim_ctx* c, int sh, const std::vector<int32_t>& L) {
     c->shape = sh;
-    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh);
+    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh, c->tile_live.data());
     drop_graphs(c);
     cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
                                     cudaMemcpyHostToDevice, c->stream);
     if (!e) e = cudaMemsetAsync(c->ws + c->lay.tile_ctr, 0, sizeof(uint32_t) * 2 * kMaxPasses, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     return cuda_check(c, e, "set shape");
+}
+
+// At an hour boundary, drop protocols that have reached their horizon from the
+// fused work list: their tiles would only be skipped, and once the survivors'
+// columns no longer fill the GPU make_tiles splits them in z again.
+sim_status refresh_tiles(sim_ctx* c) {
+    if (!c->fused() || !c->loaded) return SIM_OK;
+    std::vector<uint8_t> live(c->n);
+    bool any = false;
+    for (int p = 0; p < c->n; ++p) any |= (live[p] = c->proto[p].t_end > c->clock) != 0;
+    if (!any || live == c->tile_live) return SIM_OK;
+    c->tile_live = live;
+    std::vector<int32_t> L(c->n);
+    for (int p = 0; p < c->n; ++p) L[p] = c->proto[p].L;
+    return set_shape(c, c->shape, L);
 }
 
 }  // namespace
@@ -606,6 +631,7 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
     c->cfg = *cfg;
     c->n = n;
     c->P = make_params(*cfg);
+    c->P.frac_cap = n * cfg->max_fractions;
     c->ws = (char*)d_workspace;
     c->stream = (cudaStream_t)cuda_stream;
     int64_t site0 = 0;
@@ -646,6 +672,7 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
         }
     }
     c->tiles = make_tiles(*cfg, n, L, c->shape);
+    c->tile_live.assign(n, 1);
     int64_t nt = 0;
     for (int sh = 1; sh <= kNumShapes; ++sh) {
         const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
@@ -684,7 +711,7 @@ sim_status sim_load_protocols(sim_ctx* c, int n, const int32_t* offsets, const d
     const int F = c->cfg.max_fractions;
     const size_t cap = (size_t)n * (F > 0 ? F : 1);
     std::vector<int64_t> fstep(cap, -1);
-    std::vector<double> fdose(cap, 0.0);
+    std::vector<double> fdose(2 * cap, 0.0);  // doses, then their quadratic partners
     std::vector<Proto> proto = c->proto;
     for (int p = 0; p < n; ++p) {
         const int a = offsets[p], b = offsets[p + 1];
@@ -715,6 +742,18 @@ sim_status sim_load_protocols(sim_ctx* c, int n, const int32_t* offsets, const d
         }
         if (total > c->cfg.dose_cap_gy + 1e-9)
             return fail(c, SIM_EINVAL, "protocol " + std::to_string(p) + ": total dose above the cap");
+        // quadratic partner of each fraction: D_j + 2 sum_{i<j} D_i 2^(-(t_j - t_i) / T_half) under
+        // incomplete repair, D_j alone when repair completes between fractions
+        const double th = c->cfg.params.repair_half_h;
+        for (int j = 0; j < nf; ++j) {
+            const size_t at = (size_t)p * F + j;
+            double h = 0.0;
+            for (int i = 0; th > 0.0 && i < j; ++i) {
+                const double dt_h = (double)(fstep[at] - fstep[(size_t)p * F + i]) / kStepsPerHour;
+                h += fdose[(size_t)p * F + i] * std::exp2(-dt_h / th);
+            }
+            fdose[cap + at] = fdose[at] + 2.0 * h;
+        }
         proto[p].nfrac = nf;
         proto[p].t_end = c->cfg.t_end_steps > 0
                              ? c->cfg.t_end_steps
@@ -725,8 +764,8 @@ sim_status sim_load_protocols(sim_ctx* c, int n, const int32_t* offsets, const d
         e = cudaMemcpyAsync(c->ws + c->lay.fstep, fstep.data(), sizeof(int64_t) * cap, cudaMemcpyHostToDevice,
                             c->stream);
         if (!e)
-            e = cudaMemcpyAsync(c->ws + c->lay.fdose, fdose.data(), sizeof(double) * cap, cudaMemcpyHostToDevice,
-                                c->stream);
+            e = cudaMemcpyAsync(c->ws + c->lay.fdose, fdose.data(), sizeof(double) * 2 * cap,
+                                cudaMemcpyHostToDevice, c->stream);
     }
     if (!e)
         e = cudaMemcpyAsync(c->ws + c->lay.proto, proto.data(), sizeof(Proto) * n, cudaMemcpyHostToDevice, c->stream);
@@ -735,6 +774,40 @@ sim_status sim_load_protocols(sim_ctx* c, int n, const int32_t* offsets, const d
     c->proto = proto;
     c->loaded = true;
     return reset_device(c);
+}
+
+sim_status sim_load_dose_vectors(sim_ctx* c, const uint8_t* d_units, int n_slots, double unit_gy) {
+    if (!c) return SIM_EINVAL;
+    if (!d_units || n_slots < 1 || n_slots > (1 << 20) || !std::isfinite(unit_gy) || unit_gy <= 0.0)
+        return fail(c, SIM_EINVAL, "dose vectors: need a device pointer, 1..2^20 slots and a positive unit");
+    if (c->cfg.t_end_steps <= 0)
+        return fail(c, SIM_ESTATE, "dose vectors loaded on the device need a fixed horizon (t_end_steps > 0)");
+    if (c->cfg.max_fractions < 1) return fail(c, SIM_ESTATE, "max_fractions must be >= 1");
+    for (Proto& pr : c->proto) {
+        pr.t_end = c->cfg.t_end_steps;
+        pr.nfrac = 0;  // known on the device only
+    }
+    c->loaded = true;
+    sim_status st = reset_device(c);  // clears the status word before the loader may set it
+    if (st) return st;
+    k_load_vectors<<<(unsigned)((c->n * 32 + 255) / 256), 256, 0, c->stream>>>(
+        d_units, n_slots, unit_gy, c->n, c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.fstep),
+        c->at<double>(c->lay.fdose), c->cfg.max_fractions, c->P.frac_cap, c->cfg.dose_cap_gy,
+        c->cfg.params.repair_half_h, c->cfg.t_end_steps, c->at<uint32_t>(c->lay.status));
+    return cuda_check(c, cudaGetLastError(), "k_load_vectors launch");
+}
+
+sim_status sim_fitness_device(sim_ctx* c, int32_t* d_count, float* d_fitness) {
+    if (!c) return SIM_EINVAL;
+    cudaError_t e = cudaMemsetAsync(c->ws + c->lay.final_count, 0, sizeof(int32_t) * c->n, c->stream);
+    if (e) return cuda_check(c, e, "fitness memset");
+    k_count<<<(unsigned)c->blocks.size(), kThreads, 0, c->stream>>>(
+        c->at<Block>(c->lay.blocks), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock),
+        c->cells(c->ccur), c->at<int32_t>(c->lay.final_count), 1, 0);
+    if (sim_status st = cuda_check(c, cudaGetLastError(), "k_count launch")) return st;
+    k_fitness_out<<<(unsigned)((c->n + 255) / 256), 256, 0, c->stream>>>(
+        c->at<int32_t>(c->lay.final_count), c->n, (float)c->cfg.n_max_fitness, d_count, d_fitness);
+    return cuda_check(c, cudaGetLastError(), "k_fitness_out launch");
 }
 
 sim_status sim_reset(sim_ctx* c) {
@@ -758,6 +831,7 @@ sim_status sim_run(sim_ctx* c, int64_t max_steps) {
     sim_status st = SIM_OK;
     while (c->clock < target && st == SIM_OK) {
         st = count_hour(c);
+        if (!st && c->clock % kStepsPerHour == 0) st = refresh_tiles(c);
         if (st) break;
         if (graphs && c->clock % kStepsPerHour == 0 && c->clock + kStepsPerHour <= target) {
             st = build_hour_graph(c, c->cur, c->ccur);

@@ -37,6 +37,7 @@ struct Params {
     float phi[5];
     float O_q, G_q, H_q, G_d, H_d;
     uint32_t key0, key1, init_word;
+    int frac_cap;  // fraction-table entries per array: doses at [0, cap), quadratic partners at [cap, 2 cap)
 };
 
 struct Proto {
@@ -140,11 +141,17 @@ __device__ __forceinline__ bool is_face(int L, int x, int y, int z) {
 }
 
 // Dose delivered to protocol `pr` at `step` (fractions on one step were merged
-// on the host).  Fraction tables hold at most a few hundred entries.
+// on the host); *dq receives the dose the quadratic LQ term pairs it with (the
+// dose itself, plus twice the unrepaired dose of earlier fractions when repair
+// is incomplete).  Fraction tables hold at most a few hundred entries.
 __device__ __forceinline__ double dose_at(const Proto& pr, const int64_t* __restrict__ fstep,
-                                          const double* __restrict__ fdose, int64_t step) {
+                                          const double* __restrict__ fdose, int64_t step, int cap, double* dq) {
     for (int j = 0; j < pr.nfrac; ++j)
-        if (fstep[pr.frac0 + j] == step) return fdose[pr.frac0 + j];
+        if (fstep[pr.frac0 + j] == step) {
+            *dq = fdose[cap + pr.frac0 + j];
+            return fdose[pr.frac0 + j];
+        }
+    *dq = 0.0;
     return 0.0;
 }
 
@@ -222,13 +229,14 @@ __device__ __forceinline__ uint32_t update_cell(uint32_t w, float O, float Gv, f
 }
 
 // LQ survival of a cell of the given kind at O2 level O under dose D:
-// S = exp(-a D - b D^2), a = alpha phi OMF(O), b = beta (phi OMF)^2,
-// OMF(O) = (m O + K)/(m (O + K)).
-__device__ __forceinline__ float lq_survival(uint32_t kind, float O, float dose, const Params& P) {
+// S = exp(-a D - b D dq), a = alpha phi OMF(O), b = beta (phi OMF)^2,
+// OMF(O) = (m O + K)/(m (O + K)); dq = D with complete repair between
+// fractions, D + 2 H (H the unrepaired earlier dose) with incomplete repair.
+__device__ __forceinline__ float lq_survival(uint32_t kind, float O, float dose, float dq, const Params& P) {
     const float omf = (P.omf_m * O + P.omf_K) / (P.omf_m * (O + P.omf_K));
     const float mod = P.phi[kind - 1] * omf;
     const float a = P.alpha * mod, bq = P.beta * mod * mod;
-    return expf(-a * dose - bq * dose * dose);
+    return expf(-a * dose - bq * dose * dq);
 }
 
 }  // namespace simdev

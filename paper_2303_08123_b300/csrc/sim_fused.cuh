@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
     T* stage_f = reinterpret_cast<T*>(smem_raw);
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kStages * 3 * NC * sizeof(T));
     float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kStages * NC * (3 * sizeof(T) + sizeof(uint32_t)));
-    __shared__ float s_dose;
+    __shared__ float s_dose, s_dq;  // the step's dose and its quadratic partner
     __shared__ int s_tile;
 
     const int64_t step = *clock + k_off;
@@ -157,8 +157,10 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
     const Proto pr = protos[tl.p];
     if (step >= pr.t_end) continue;
     if (threadIdx.x == 0) {
-        const double d = first ? dose_at(pr, fstep, fdose, step) : 0.0;
+        double q = 0.0;
+        const double d = first ? dose_at(pr, fstep, fdose, step, P.frac_cap, &q) : 0.0;
         s_dose = (float)d;
+        s_dq = (float)q;
         if (d > 0.0 && tl.x0 == 0 && tl.y0 == 0 && tl.z0 == 0) cum_dose[tl.p] += d;  // one tile per protocol
     }
     const int L = pr.L;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
                 const bool fl = ln ? fb : fa;
                 const uint32_t kind = wl & kKindMask;
                 if (fl || kind == kEmpty) continue;
-                const float Sv = lq_survival(kind, ln ? v0[0].y : v0[0].x, dose, P);
+                const float Sv = lq_survival(kind, ln ? v0[0].y : v0[0].x, dose, s_dq, P);
                 const int s = xa + ln + L * y + LL * i;
                 const uint4 r = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)step, kPurposeIrr, (uint32_t)tl.p),
                                               P.key0, P.key1);
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
     float* stage_f = reinterpret_cast<float*>(smem_raw);
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * 3 * NC * sizeof(float));
     float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float));
-    __shared__ float s_dose;
+    __shared__ float s_dose, s_dq;  // the step's dose and its quadratic partner
     __shared__ int s_tile;
 
     const int tid = threadIdx.x;
@@ -469,8 +471,10 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
     const Proto pr = protos[tl.p];
     if (step >= pr.t_end) continue;
     if (threadIdx.x == 0) {
-        const double d = first ? dose_at(pr, fstep, fdose, step) : 0.0;
+        double q = 0.0;
+        const double d = first ? dose_at(pr, fstep, fdose, step, P.frac_cap, &q) : 0.0;
         s_dose = (float)d;
+        s_dq = (float)q;
         if (d > 0.0 && tl.x0 == 0 && tl.y0 == 0 && tl.z0 == 0) cum_dose[tl.p] += d;
     }
     const int L = pr.L;
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
             w = my_cell[st * NC];
         }
         if (dose > 0.f && loaded && !fxy && i > 0 && i < L - 1 && (w & kKindMask) != kEmpty) {
-            const float Sv = lq_survival(w & kKindMask, v0[0], dose, P);
+            const float Sv = lq_survival(w & kKindMask, v0[0], dose, s_dq, P);
             const int s = x + L * y + LL * i;
             const uint4 r = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)step, kPurposeIrr, (uint32_t)tl.p),
                                           P.key0, P.key1);

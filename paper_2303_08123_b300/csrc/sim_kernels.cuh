@@ -72,16 +72,19 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
     const Proto pr = protos[b.p];
     const int64_t step = *clock + k_off;
     if (step >= pr.t_end) return;
-    float dose = 0.f;
+    float dose = 0.f, dq = 0.f;
     if (sub == 0) {  // the step's fraction is applied in its first substep
-        __shared__ float s_dose;
+        __shared__ float s_dose, s_dq;
         if (threadIdx.x == 0) {
-            const double d = dose_at(pr, fstep, fdose, step);
+            double q;
+            const double d = dose_at(pr, fstep, fdose, step, P.frac_cap, &q);
             s_dose = (float)d;
+            s_dq = (float)q;
             if (d > 0.0 && b.begin == 0) cum_dose[b.p] += d;  // exactly one block per protocol has begin == 0
         }
         __syncthreads();
         dose = s_dose;
+        dq = s_dq;
     }
     const int L = pr.L;
     const int64_t LL = (int64_t)L * L;
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
         uint32_t w = cell[g];
         const uint32_t kind = w & kKindMask;
         if (dose > 0.f && kind != kEmpty) {
-            const float S = lq_survival(kind, O, dose, P);
+            const float S = lq_survival(kind, O, dose, dq, P);
             const uint4 r = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)step, kPurposeIrr, (uint32_t)b.p),
                                           P.key0, P.key1);
             if (u24(r.x) >= S) {
@@ -353,6 +356,65 @@ __global__ void k_totals_finish(const int32_t* __restrict__ first_block, int n, 
     }
     out64[idx] = a;
     out32[idx] = sum;
+}
+
+// ---------------------------------------------------------------------------
+// Dose vectors on the device -> fraction tables ("Protocol Representation":
+// entry i of a protocol's vector is the dose i * 30 min after the start, i.e.
+// at step 300 i).  One warp per protocol compacts the non-zero entries in slot
+// order (ballot + popc), checks the fraction count and the dose cap, and
+// fills the quadratic LQ partner of each fraction (incomplete repair with
+// half-time half_h > 0, the dose itself otherwise).  A protocol that breaks a
+// limit gets no fractions and raises bit kStatusBadProtocol of *status.
+constexpr uint32_t kStatusBadProtocol = 2u;
+constexpr int kStepsPerSlot = 300;
+
+__global__ void k_load_vectors(const uint8_t* __restrict__ units, int S, double unit_gy, int n,
+                               Proto* __restrict__ protos, int64_t* __restrict__ fstep, double* __restrict__ fdose,
+                               int F, int cap, double dose_cap, double half_h, int64_t t_end,
+                               uint32_t* __restrict__ status) {
+    const int p = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (p >= n) return;
+    const uint8_t* row = units + (size_t)p * S;
+    const int f0 = protos[p].frac0;
+    int nf = 0, total = 0;
+    for (int base = 0; base < S; base += 32) {
+        const int s = base + lane;
+        const int u = s < S ? row[s] : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, u != 0);
+        const int pos = nf + __popc(m & ((1u << lane) - 1u));
+        if (u && pos < F) {
+            fstep[f0 + pos] = (int64_t)s * kStepsPerSlot;
+            fdose[f0 + pos] = u * unit_gy;
+        }
+        nf += __popc(m);
+        total += __reduce_add_sync(0xffffffffu, u);
+    }
+    const bool bad = nf > F || total * unit_gy > dose_cap + 1e-9;
+    if (bad) nf = 0;
+    __syncwarp();
+    for (int j = lane; j < nf; j += 32) {
+        double h = 0.0;
+        for (int i = 0; half_h > 0.0 && i < j; ++i) {
+            const double dt_h = (double)(fstep[f0 + j] - fstep[f0 + i]) / kStepsPerHour;
+            h += fdose[f0 + i] * exp2(-dt_h / half_h);
+        }
+        fdose[cap + f0 + j] = fdose[f0 + j] + 2.0 * h;
+    }
+    if (lane == 0) {
+        protos[p].nfrac = nf;
+        protos[p].t_end = t_end;
+        if (bad) atomicOr(status, kStatusBadProtocol);
+    }
+}
+
+// final count and fitness n_max - n per protocol into device arrays
+__global__ void k_fitness_out(const int32_t* __restrict__ count, int n, float n_max, int32_t* __restrict__ d_count,
+                              float* __restrict__ d_fit) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (d_count) d_count[p] = count[p];
+    if (d_fit) d_fit[p] = n_max - (float)count[p];
 }
 
 }  // namespace simdev

@@ -36,7 +36,7 @@ class SimParams(ctypes.Structure):
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("omf_m", ctypes.c_double),
         ("omf_K", ctypes.c_double), ("phi", ctypes.c_double * 5),
         ("O_q", ctypes.c_double), ("G_q", ctypes.c_double), ("pH_q", ctypes.c_double),
-        ("G_d", ctypes.c_double), ("pH_d", ctypes.c_double),
+        ("G_d", ctypes.c_double), ("pH_d", ctypes.c_double), ("repair_half_h", ctypes.c_double),
     ]
 
 
@@ -58,7 +58,7 @@ def pack_params(p: Params) -> SimParams:
     for i in range(3):
         s.lam[i] = p.lam[i]
     for n in ("medium_O", "medium_G", "medium_pH", "q_O", "K_O", "q_G", "K_G", "k_an", "O_an", "q_H", "f_Q",
-              "alpha", "beta", "omf_m", "omf_K", "O_q", "G_q", "pH_q", "G_d", "pH_d"):
+              "alpha", "beta", "omf_m", "omf_K", "O_q", "G_q", "pH_q", "G_d", "pH_d", "repair_half_h"):
         setattr(s, n, float(getattr(p, n)))
     for i in range(5):
         s.phi[i] = p.phi[i]
@@ -77,6 +77,8 @@ SIGNATURES = {
                                   _P(_vp)]),
     "sim_load_protocols": (ctypes.c_int, [_vp, ctypes.c_int, _i32p, _f64p, _f64p]),
     "sim_reset": (ctypes.c_int, [_vp]),
+    "sim_load_dose_vectors": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double]),
+    "sim_fitness_device": (ctypes.c_int, [_vp, _vp, _vp]),
     "sim_run": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "sim_fitness": (ctypes.c_int, [_vp, _i32p, _f64p]),
     "sim_counts": (ctypes.c_int, [_vp, _i32p, ctypes.c_int]),
@@ -207,6 +209,25 @@ class Simulator:
 
     def run(self, max_steps: int = 0):
         self._call("sim_run", int(max_steps))
+
+    def load_dose_vectors(self, units, unit_gy: float = 0.25):
+        """Protocols from a device uint8 tensor [n, n_slots] of dose units per
+        30-min slot (asynchronous; keep `units` alive until the stream passes)."""
+        import torch
+        if not (units.is_cuda and units.dtype == torch.uint8 and units.dim() == 2 and units.is_contiguous()
+                and units.shape[0] == self.n):
+            raise ValueError("units must be a contiguous CUDA uint8 tensor of shape [n_protocols, n_slots]")
+        self._call("sim_load_dose_vectors", ctypes.c_void_p(units.data_ptr()), int(units.shape[1]), float(unit_gy))
+
+    def fitness_device(self, count=None, fitness=None):
+        """Final counts (int32) and fitness n_max - n (float32) into device
+        tensors on the stream, without synchronising; returns (count, fitness)."""
+        import torch
+        dev = self.workspace.device
+        count = torch.empty(self.n, dtype=torch.int32, device=dev) if count is None else count
+        fitness = torch.empty(self.n, dtype=torch.float32, device=dev) if fitness is None else fitness
+        self._call("sim_fitness_device", ctypes.c_void_p(count.data_ptr()), ctypes.c_void_p(fitness.data_ptr()))
+        return count, fitness
 
     def fitness(self):
         cnt = np.zeros(self.n, dtype=np.int32)

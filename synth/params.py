@@ -65,6 +65,8 @@ class Params:
     pH_q: float = 6.8
     G_d: float = 0.02
     pH_d: float = 6.4
+    # sublethal-damage repair half-time (h); 0 = complete repair between fractions
+    repair_half_h: float = 0.0
     flags: int = F_DEFAULT
 
     def replace(self, **kw) -> "Params":

@@ -99,3 +99,33 @@ def test_mlp_library_exports_every_declared_symbol():
     size = ctypes.c_size_t()
     assert lib.mlp_workspace_size(100, ctypes.byref(size)) == -1  # batches are multiples of 128
     assert lib.mlp_workspace_size(256, ctypes.byref(size)) == 0 and size.value > 0
+
+
+def test_ga_library_exports_and_layout(tmp_path):
+    """libga exports what ga.h declares, the binding mirrors ga_params, and bad
+    arguments are rejected before any device work."""
+    from paper_2303_08123_b300 import _build
+    _build.build()
+    from paper_2303_08123_b300.devga import SIGNATURES, GaParams, load_library, make_params
+    lib = load_library()
+    for n in declared("ga.h"):
+        assert hasattr(lib, n) and n in SIGNATURES, n
+    fields = [f for f, _ in GaParams._fields_]
+    src = tmp_path / "ga_layout.c"
+    src.write_text("\n".join(['#include <stdio.h>', '#include <stddef.h>', '#include "ga.h"', 'int main(void){',
+                              'printf("%zu\\n", sizeof(ga_params));']
+                             + [f'printf("%zu\\n", offsetof(ga_params, {f}));' for f in fields] + ["return 0;}"]))
+    exe = tmp_path / "ga_layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).decode().split()]
+    assert vals == [ctypes.sizeof(GaParams)] + [getattr(GaParams, f).offset for f in fields]
+    size = ctypes.c_size_t()
+    assert lib.ga_workspace_size(0, ctypes.byref(size)) == -1
+    assert lib.ga_workspace_size(4096, ctypes.byref(size)) == 0 and size.value >= 16 * 4096
+    ok = make_params()
+    for bad in (dict(n_slots=0), dict(n_slots=2000), dict(d_max=0), dict(min_gap=0), dict(n_parents=0),
+                dict(selection=3), dict(crossover=7), dict(mutations=16), dict(p_mut=1.5),
+                dict(selection=2, tournament_k=65)):
+        p = make_params(**bad)
+        assert lib.ga_random_population(ctypes.byref(p), 64, 1, ctypes.c_void_p(1), None) == -1, bad
+    assert lib.ga_generation(ctypes.byref(ok), 64, None, None, 1, 0, None, None, None, 0, None) == -1

@@ -320,3 +320,60 @@ def test_ragged_batch_persistent_fused_equals_substep_and_oracle(cuda, orc):
         ref = orc.run(P0, int(L[p]), int(R[p]), SEED, p, prot[p][0], prot[p][1], t_end_steps=1200, hours=2)
         assert np.array_equal(out[1][0][p], ref["state"].cell), p
         assert np.array_equal(out[1][1][p], ref["counts"])
+
+
+def test_retiring_protocols_leave_the_work_list(cuda, orc):
+    """Staggered horizons (1-5 h): as protocols reach their horizon the fused
+    work list is rebuilt from the survivors at hour boundaries.  The batch run
+    to its end equals the substep path bit for bit, a retired protocol stays
+    frozen at its horizon state (oracle), and a reset run repeats exactly."""
+    from paper_2303_08123_b300 import csr
+    n = 12
+    prot = [([1.0 + 0.5 * (p % 3)], [0.5 + 0.5 * (p % 9)]) for p in range(n)]
+    L, R = [16 + 8 * (p % 2) for p in range(n)], [3 + (p % 2) for p in range(n)]
+    out = []
+    for kw in (dict(path="substep"), dict(path="fused", tile_shape=4)):
+        sim = _sim(L, R, hours=6, regrowth_h=1, **kw)
+        sim.load_protocols(*csr(prot))
+        sim.run(0)
+        first = ([sim.get_state(p)[3] for p in range(n)], sim.counts())
+        if kw["path"] == "fused":
+            sim.reset()
+            sim.run(0)
+            for a, b in zip(first[0], [sim.get_state(p)[3] for p in range(n)]):
+                assert np.array_equal(a, b)
+            assert np.array_equal(first[1], sim.counts())
+        out.append(first)
+        sim.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1], out[1][1])
+    for p in (0, 8):  # retires mid-hour (step 900) while the others run on; the last to retire
+        ref = orc.run(P0, L[p], R[p], SEED, p, prot[p][0], prot[p][1], regrowth_h=1, hours=6)
+        assert np.array_equal(out[1][0][p], ref["state"].cell), p
+        assert np.array_equal(out[1][1][p], ref["counts"]), p
+
+
+@pytest.mark.parametrize("path", ["fused", "substep"])
+def test_incomplete_repair_parity(cuda, orc, path):
+    """Incomplete repair between fractions (half-time 1 h): three close fractions
+    on two protocols, whole runs equal the oracle (cells bit-exact, counts equal),
+    and the interaction term really acts (more kills than with complete repair)."""
+    from paper_2303_08123_b300 import csr
+    L, R, T = 24, 6, 2100
+    prot = [([2.0, 2.5, 2.0], [0.5, 1.0, 1.0]), ([1.5, 3.0, 1.0], [0.5, 0.5, 1.5])]
+    p_rep = P0.replace(repair_half_h=1.0)
+    kills = []
+    for p in (P0, p_rep):
+        sim = _sim([L, L], [R, R], hours=3, t_end_steps=T, params=p, path=path)
+        sim.load_protocols(*csr(prot))
+        sim.run(0)
+        cells = [sim.get_state(i)[3] for i in range(2)]
+        kills.append(sim.counts()[:, 3])
+        if p is p_rep:
+            for i in range(2):
+                ref = orc.run(p, L, R, SEED, i, prot[i][0], prot[i][1], t_end_steps=T, hours=3)
+                assert np.array_equal(cells[i], ref["state"].cell), (i, ref["stats"])
+                assert np.array_equal(sim.counts()[i], ref["counts"]), i
+        sim.close()
+    assert kills[1].sum() < kills[0].sum()

@@ -231,6 +231,39 @@ def test_lq_survival_inside_binomial_ci(orc, kind, O, D):
         assert math.isclose(-math.log(S_), p.alpha * p.phi[0] / p.omf_m * D + p.beta * (p.phi[0] / p.omf_m * D) ** 2)
 
 
+@pytest.mark.parametrize("half_h,doses,waits", [
+    (0.0, [3.0, 3.0], [0.0, 1.0]),              # complete repair: independent fractions
+    (0.5, [3.0, 3.0], [0.0, 1.0]),              # theta = 2^-2
+    (1e9, [3.0, 3.0], [0.0, 1.0]),              # no repair: the quadratic term of one 6 Gy dose
+    (1.0, [2.0, 3.0, 2.5], [0.0, 1.0, 0.5]),    # three fractions, three distinct decay factors
+])
+def test_incomplete_repair_matches_closed_form(orc, half_h, doses, waits):
+    """Fractions D_i at times t_i on a uniform oxic lattice (phase factors 1, no
+    division): the fraction of cells neither doomed nor dead after the last
+    fraction lies inside the 99.9 % binomial interval of the incomplete-repair
+    LQ survival exp(-a sum D_i - b (sum D_i^2 + 2 sum_{i<j} theta_ij D_i D_j)),
+    theta_ij = 2^(-(t_j - t_i) / T_half) (Thames 1985)."""
+    L, R = 48, 40  # the ball covers every interior site
+    p = P0.replace(flags=0, n_sub=0, phi=(1.0,) * 5, repair_half_h=half_h)
+    steps = np.cumsum(np.array(waits) * 600).astype(int)
+    ref = orc.run(p, L, R, SEED, 7, doses, waits, t_end_steps=int(steps[-1]) + 1)
+    N0 = (L - 2) ** 3
+    alive = (ref["state"].cell & 7) != EMPTY
+    n_ok = int(np.count_nonzero(alive & ((ref["state"].cell & 8) == 0)))
+    O = p.medium_O
+    omf = (p.omf_m * O + p.omf_K) / (p.omf_m * (O + p.omf_K))
+    a, b = p.alpha * omf, p.beta * omf * omf
+    t = np.array(waits).cumsum()
+    quad = sum(d * d for d in doses)
+    for j in range(len(doses)):
+        for i in range(j):
+            theta = 0.0 if half_h == 0 else 2.0 ** (-(t[j] - t[i]) / half_h)
+            quad += 2 * theta * doses[i] * doses[j]
+    S_ = math.exp(-a * sum(doses) - b * quad)
+    half = 3.29 * math.sqrt(S_ * (1 - S_) / N0)
+    assert abs(n_ok / N0 - S_) <= half, (n_ok / N0, S_, half)
+
+
 def test_doomed_cells_die_at_mitosis(orc):
     """A lethally hit cell keeps cycling and dies when it completes M."""
     L = 6
