@@ -78,7 +78,7 @@ Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nb
 bool valid_config(const sim_config* cfg, std::string* why) {
     const sim_params& p = cfg->params;
     if (cfg->precision < SIM_FP32 || cfg->precision > SIM_FP16) return *why = "precision must be 0, 1 or 2", false;
-    if (p.n_sub < 1 || p.n_sub > 64) return *why = "n_sub must be in 1..64", false;
+    if (p.n_sub < 1 || p.n_sub > 256) return *why = "n_sub must be in 1..256", false;
     for (int i = 0; i < 4; ++i) {
         const double st = p.dur_h[i] * kStepsPerHour;
         if (!(st >= 1.0) || st > 1e8) return *why = "phase durations must be at least one step", false;

@@ -185,13 +185,20 @@ __device__ __forceinline__ float stencil_t(float c, float xm, float xp, float ym
 // Uptake of one substep by a cell of the given kind:
 //   U_O = f q_O O/(O+K_O);  g = f q_G G/(G+K_G);  w = O_an/(O+O_an)
 //   U_G = g (1 + (k_an-1) w);  H+ release = q_H g k_an w
-// with f = 1 for cycling and f_Q for quiescent cells.
+// with f = 1 for cycling and f_Q for quiescent cells.  The three quotients
+// share one fast reciprocal: with a = O+K_O, b = O+O_an, c = G+K_G and
+// r ~ 1/(a b c), O/a = O (b c) r, G/c = G (a b) r and O_an/b = O_an (a c) r.
+// a b c lies in [K_O O_an K_G, ~0.5] (normal floats), so the relative error
+// stays at a few FP32 ulps, far inside the per-step field tolerance.
 __device__ __forceinline__ void uptake(uint32_t kind, float O, float Gv, const Params& P, float& uO, float& uG,
                                        float& pH) {
     const float f = (kind == kQ) ? P.f_Q : 1.f;
-    uO = __fdiv_rn(__fmul_rn(__fmul_rn(f, P.q_O), O), __fadd_rn(O, P.K_O));
-    const float gg = __fdiv_rn(__fmul_rn(__fmul_rn(f, P.q_G), Gv), __fadd_rn(Gv, P.K_G));
-    const float wa = __fdiv_rn(P.O_an, __fadd_rn(O, P.O_an));
+    const float a = __fadd_rn(O, P.K_O), b = __fadd_rn(O, P.O_an), c = __fadd_rn(Gv, P.K_G);
+    const float ab = __fmul_rn(a, b);
+    const float r = __fdividef(1.f, __fmul_rn(ab, c));
+    uO = __fmul_rn(__fmul_rn(__fmul_rn(f, P.q_O), O), __fmul_rn(__fmul_rn(b, c), r));
+    const float gg = __fmul_rn(__fmul_rn(__fmul_rn(f, P.q_G), Gv), __fmul_rn(ab, r));
+    const float wa = __fmul_rn(P.O_an, __fmul_rn(__fmul_rn(a, c), r));
     uG = __fmul_rn(gg, __fmaf_rn(__fsub_rn(P.k_an, 1.f), wa, 1.f));
     pH = __fmul_rn(__fmul_rn(__fmul_rn(P.q_H, gg), P.k_an), wa);
 }

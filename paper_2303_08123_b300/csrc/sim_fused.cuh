@@ -109,7 +109,7 @@ template <>
 __device__ __forceinline__ float lds1<__half>(const __half* p) { return __half2float(*p); }
 
 constexpr int kDepth = 4;              // planes in flight per CTA
-constexpr int kMaxPasses = 32;         // tile-ticket slots per step parity (n_sub <= 64)
+constexpr int kMaxPasses = 128;        // tile-ticket slots per step parity (n_sub <= 256)
 
 // Persistent scheduling: each CTA takes tiles by atomic ticket from the slot
 // of this (step parity, pass); the division-resolve kernel of a step clears

@@ -74,3 +74,13 @@ class Params:
 
 
 P0 = Params()
+
+# Physical-rate diffusion variant (build reading, not the paper's numbers):
+# oxygen spreads D dt / dx^2 ~ 20-50 lattice units per 6 s step at 10-20 um
+# sites, far more than P0's coarse-grained 4 x 0.15.  Modelled with many
+# explicit substeps at P0's per-substep lambda (O2: 128 x 0.15 = 19.2 per
+# step) and the per-substep uptake scaled by 4/128, so that a cell consumes
+# per step what it consumes under P0 while the fields relax towards their
+# quasi-steady profile within each step.
+P_PHYS = P0.replace(n_sub=128, q_O=P0.q_O * 4 / 128, q_G=P0.q_G * 4 / 128)
+

@@ -377,3 +377,29 @@ def test_incomplete_repair_parity(cuda, orc, path):
                 assert np.array_equal(sim.counts()[i], ref["counts"]), i
         sim.close()
     assert kills[1].sum() < kills[0].sum()
+
+
+def test_physical_rate_variant(cuda, orc):
+    """128 substeps per step (physical-rate diffusion reading): 64 fused passes
+    per step equal the substep path bit for bit, and the oracle (cells
+    bit-exact, fields within 1e-4 of the medium value) after 30 steps."""
+    from paper_2303_08123_b300 import csr
+    from synth.params import P_PHYS
+    L, R, T = [16, 24], [3, 4], 30
+    prot = [([2.0], [0.0]), ([1.0], [0.0])]
+    out = []
+    for path in ("substep", "fused"):
+        sim = _sim(L, R, hours=1, t_end_steps=T, params=P_PHYS, path=path)
+        sim.load_protocols(*csr(prot))
+        sim.run(0)
+        out.append([sim.get_state(p) for p in range(2)])
+        sim.close()
+    for a, b in zip(out[0], out[1]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    for p in range(2):
+        ref = orc.run(P_PHYS, L[p], R[p], SEED, p, prot[p][0], prot[p][1], t_end_steps=T)
+        O, G, H, cell = out[1][p]
+        assert np.array_equal(cell, ref["state"].cell), (p, ref["stats"])
+        for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
+            assert np.max(np.abs(g - o)) / m < 1e-4
