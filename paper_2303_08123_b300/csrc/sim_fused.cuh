@@ -72,6 +72,18 @@ __device__ __forceinline__ float2 stencil_t2(float2 c, float2 xm, float2 xp, flo
     return __ffma2_rn(f2(lam, lam), lap, c);
 }
 
+// the same sequence on two fields of one site (O2 and glucose), each with its own lambda
+__device__ __forceinline__ float2 stencil_t2l(float2 c, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm,
+                                              float2 zp, float2 lam) {
+    float2 s = __fadd2_rn(xm, xp);
+    s = __fadd2_rn(s, ym);
+    s = __fadd2_rn(s, yp);
+    s = __fadd2_rn(s, zm);
+    s = __fadd2_rn(s, zp);
+    const float2 lap = __ffma2_rn(f2(-6.f, -6.f), c, s);
+    return __ffma2_rn(lam, lap, c);
+}
+
 // ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies (cp.async), zero-filled where the source
 // lies outside the lattice.  Used to keep kDepth planes in flight per CTA.
@@ -410,8 +422,10 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
 // ---------------------------------------------------------------------------
 // One column per thread (FP32 storage only): the same pipeline as k_fused with
 // twice the threads per tile, for latency-bound shapes where more resident
-// warps matter more than packed arithmetic.  Same pinned arithmetic, so the
-// results are bit-identical to the other paths.
+// warps matter more than column pairs.  O2 and glucose of a site sit side by
+// side in shared memory (float2), so one 8-byte load fetches both and their
+// stencils run as packed f32x2 operations; H+ stays scalar.  Same pinned
+// arithmetic, so the results are bit-identical to the other paths.
 template <int TX, int TY, int K>
 struct FusedShape1 {
     static constexpr int HX = TX + 2 * K, HY = TY + 2 * K, NC = HX * HY;
@@ -420,6 +434,7 @@ struct FusedShape1 {
 
 constexpr int kStages1 = 8;  // stages of the one-column kernel (a power of two >= kDepth + 2)
 
+// stages: (O2, glucose) float2, H+ float, cell word per site; level planes: float2 + float per site
 template <int TX, int TY, int K>
 constexpr size_t fused1_smem_bytes() {
     using S = FusedShape1<TX, TY, K>;
@@ -442,9 +457,12 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
     constexpr int HX = S::HX, HY = S::HY, NC = S::NC;
     constexpr int kS1 = kStages1;  // power of two: stage index = (plane - zl0) & (kS1 - 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stage_f = reinterpret_cast<float*>(smem_raw);
-    uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * 3 * NC * sizeof(float));
-    float* slv = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float));
+    float2* stage_og = reinterpret_cast<float2*>(smem_raw);
+    float* stage_h = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * sizeof(float2));
+    uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * NC * 3 * sizeof(float));
+    float2* lv_og = reinterpret_cast<float2*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float));
+    float* lv_h = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float) +
+                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NC * sizeof(float2));
     __shared__ float s_dose, s_dq;  // the step's dose and its quadratic partner
     __shared__ int s_tile;
 
@@ -456,9 +474,12 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
 #pragma unroll
     for (int l = 1; l <= K; ++l) inreg[l] = act && cx >= l && cx < HX - l && cy >= l && cy < HY - l;
     const bool outtile = act && cx >= K && cx < K + TX && cy >= K && cy < K + TY;
-    float* const my_stage = stage_f + tid;     // + s * 3 * NC + f * NC
+    float2* const my_og = stage_og + tid;      // + s * NC
+    float* const my_h = stage_h + tid;         // + s * NC
     uint32_t* const my_cell = stage_c + tid;   // + s * NC
-    float* const my_lv = slv + tid;            // + ((l - 1) * 2 + parity) * 3 * NC + f * NC
+    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NC
+    float* const my_lvh = lv_h + tid;          // + ((l - 1) * 2 + parity) * NC
+    const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
     const bool diffuse = (P.flags & kFDiffusion) != 0, react = (P.flags & kFReaction) != 0;
 
@@ -496,22 +517,24 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
         if (fetch && j <= zl1) {
             const int s = (j - zl0) & (kS1 - 1);
             const int o = j * LL;
-            float* sf = my_stage + s * 3 * NC;
-            cp_async(sf, g0 + o, 4, in);
-            cp_async(sf + NC, g1 + o, 4, in);
-            cp_async(sf + 2 * NC, g2 + o, 4, in);
+            float2* sog = my_og + s * NC;
+            cp_async(&sog->x, g0 + o, 4, in);
+            cp_async(&sog->y, g1 + o, 4, in);
+            cp_async(my_h + s * NC, g2 + o, 4, in);
             cp_async(my_cell + s * NC, gC + o, 4, in);
         }
         cp_async_commit();
     };
 
-    float ring[K][3][3];
+    float2 rog[K][3];  // z-rings per level: (O2, glucose) and H+
+    float rh[K][3];
 #pragma unroll
     for (int l = 0; l < K; ++l)
 #pragma unroll
-        for (int f = 0; f < 3; ++f)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) ring[l][f][j] = 0.f;
+        for (int j = 0; j < 3; ++j) {
+            rog[l][j] = f2(0.f, 0.f);
+            rh[l][j] = 0.f;
+        }
     uint32_t wr[3] = {0u, 0u, 0u};
     uint32_t hit = 0;
 
@@ -520,24 +543,29 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
     __syncthreads();
     const float dose = s_dose;
     const int n_it = zl1 + K - zl0 + 1;
-    auto iteration = [&](auto phc, const int i) {
+    // Planes i in [i_lo, i_hi] need none of the z-boundary checks (loaded, in
+    // the level ranges, no face plane, inside the tile's output range); the
+    // iterations there run a CHK = false instance without them.
+    const int i_lo = max(max(zl0 + 2 * K, z0 + K), K + 1);
+    const int i_hi = min(min(zl1, z1 - 1 + K), L - 2);
+    auto iteration = [&](auto phc, auto chkc, const int i) {
         constexpr int ph = decltype(phc)::value;
+        constexpr bool CHK = decltype(chkc)::value;
         cp_async_wait<kDepth - 1>();
         __syncthreads();
         prefetch(i + kDepth);
-        const bool loaded = i <= zl1;
+        const bool loaded = !CHK || i <= zl1;
         const int st = (i - zl0) & (kS1 - 1);
-        float v0[3] = {0.f, 0.f, 0.f};
+        float2 v0og = f2(0.f, 0.f);
+        float v0h = 0.f;
         uint32_t w = 0;
         if (loaded && act) {
-            const float* sf = my_stage + st * 3 * NC;
-            v0[0] = sf[0];
-            v0[1] = sf[NC];
-            v0[2] = sf[2 * NC];
+            v0og = my_og[st * NC];
+            v0h = my_h[st * NC];
             w = my_cell[st * NC];
         }
-        if (dose > 0.f && loaded && !fxy && i > 0 && i < L - 1 && (w & kKindMask) != kEmpty) {
-            const float Sv = lq_survival(w & kKindMask, v0[0], dose, s_dq, P);
+        if (dose > 0.f && loaded && !fxy && (!CHK || (i > 0 && i < L - 1)) && (w & kKindMask) != kEmpty) {
+            const float Sv = lq_survival(w & kKindMask, v0og.x, dose, s_dq, P);
             const int s = x + L * y + LL * i;
             const uint4 r = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)step, kPurposeIrr, (uint32_t)tl.p),
                                           P.key0, P.key1);
@@ -548,60 +576,69 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
             }
         }
         wr[ph] = w;
-#pragma unroll
-        for (int f = 0; f < 3; ++f) ring[0][f][ph] = v0[f];
+        rog[0][ph] = v0og;
+        rh[0][ph] = v0h;
 #pragma unroll
         for (int l = 1; l <= K; ++l) {
             const int q = i - l;
             const int sq = (ph - l + 6) % 3, sm = (ph - l - 1 + 6) % 3, sp = (ph - l + 1 + 6) % 3;
-            const int lo = (zl0 == 0) ? 0 : zl0 + l;
-            const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
-            const bool reg = inreg[l] && q >= lo && q <= hi;
-            float v[3] = {0.f, 0.f, 0.f};
+            bool reg = inreg[l];
+            if constexpr (CHK) {
+                const int lo = (zl0 == 0) ? 0 : zl0 + l;
+                const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
+                reg = reg && q >= lo && q <= hi;
+            }
+            float2 vog = f2(0.f, 0.f);
+            float vh = 0.f;
             if (reg) {
-                if (fxy || q == 0 || q == L - 1) {
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) v[f] = ring[l - 1][f][sq];
+                const float2 cog = rog[l - 1][sq];
+                const float ch = rh[l - 1][sq];
+                if (fxy || (CHK && (q == 0 || q == L - 1))) {
+                    vog = cog;
+                    vh = ch;
                 } else {
                     // level l-1 plane q: the stage of plane q (l = 1) or the shared plane of level l-1
-                    const float* pl = (l == 1) ? my_stage + ((q - zl0) & (kS1 - 1)) * 3 * NC
-                                               : my_lv + ((l >= 2 ? l - 2 : 0) * 2 + (q & 1)) * 3 * NC;
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        const float c = ring[l - 1][f][sq];
-                        const float* pf = pl + f * NC;
-                        v[f] = diffuse ? stencil_t(c, pf[-1], pf[1], pf[-HX], pf[HX], ring[l - 1][f][sm],
-                                                   ring[l - 1][f][sp], P.lam[f])
-                                       : c;
+                    const int pj = (l == 1) ? ((q - zl0) & (kS1 - 1)) : ((l >= 2 ? l - 2 : 0) * 2 + (q & 1));
+                    const float2* pog = ((l == 1) ? my_og : my_lvog) + pj * NC;
+                    const float* phh = ((l == 1) ? my_h : my_lvh) + pj * NC;
+                    if (diffuse) {
+                        vog = stencil_t2l(cog, pog[-1], pog[1], pog[-HX], pog[HX], rog[l - 1][sm], rog[l - 1][sp],
+                                          lam_og);
+                        vh = stencil_t(ch, phh[-1], phh[1], phh[-HX], phh[HX], rh[l - 1][sm], rh[l - 1][sp],
+                                       P.lam[2]);
+                    } else {
+                        vog = cog;
+                        vh = ch;
                     }
                     float uO = 0.f, uG = 0.f, pHv = 0.f;
                     const uint32_t kq = wr[sq] & kKindMask;
-                    if (react && kq != kEmpty) uptake(kq, ring[l - 1][0][sq], ring[l - 1][1][sq], P, uO, uG, pHv);
-                    v[0] = fmaxf(__fsub_rn(v[0], uO), 0.f);
-                    v[1] = fmaxf(__fsub_rn(v[1], uG), 0.f);
-                    v[2] = fmaxf(__fadd_rn(v[2], pHv), 0.f);
+                    if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
+                    const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));  // v - u, lane by lane
+                    vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
+                    vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
                 }
             }
             if (l < K) {
-                float* dst = my_lv + ((l - 1) * 2 + (q & 1)) * 3 * NC;
-#pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    ring[l][f][sq] = v[f];
-                    if (act) dst[f * NC] = v[f];
+                const int pj = (l - 1) * 2 + (q & 1);
+                rog[l][sq] = vog;
+                rh[l][sq] = vh;
+                if (act) {
+                    my_lvog[pj * NC] = vog;
+                    my_lvh[pj * NC] = vh;
                 }
             } else {
                 bool want = false;
                 const int o = q * LL;
-                if (outc && q >= z0 && q < z1) {
-                    const bool face = fxy || q == 0 || q == L - 1;
+                if (outc && (!CHK || (q >= z0 && q < z1))) {
+                    const bool face = fxy || (CHK && (q == 0 || q == L - 1));
                     const int64_t g = pr.site0 + col + o;
                     if (!face) {
-                        oO[g] = v[0];
-                        oG[g] = v[1];
-                        oH[g] = v[2];
+                        oO[g] = vog.x;
+                        oG[g] = vog.y;
+                        oH[g] = vh;
                     }
                     const uint32_t w0 = wr[sq];
-                    if (EPI) cout[g] = face ? w0 : update_cell(w0, v[0], v[1], v[2], P, want);
+                    if (EPI) cout[g] = face ? w0 : update_cell(w0, vog.x, vog.y, vh, P, want);
                     else if (hit >> sq & 1u) cout[g] = w0;
                 }
                 hit &= ~(1u << sq);
@@ -618,10 +655,26 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 2
             }
         }
     };
-    for (int ib = 0; ib < n_it; ib += 3) {
-        iteration(std::integral_constant<int, 0>{}, zl0 + ib);
-        if (ib + 1 < n_it) iteration(std::integral_constant<int, 1>{}, zl0 + ib + 1);
-        if (ib + 2 < n_it) iteration(std::integral_constant<int, 2>{}, zl0 + ib + 2);
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using Checked = std::integral_constant<bool, true>;
+    using Unchecked = std::integral_constant<bool, false>;
+    int ib = 0;
+    for (; ib < n_it && zl0 + ib < i_lo; ib += 3) {
+        iteration(I0{}, Checked{}, zl0 + ib);
+        if (ib + 1 < n_it) iteration(I1{}, Checked{}, zl0 + ib + 1);
+        if (ib + 2 < n_it) iteration(I2{}, Checked{}, zl0 + ib + 2);
+    }
+    for (; ib + 2 < n_it && zl0 + ib + 2 <= i_hi; ib += 3) {  // every plane of the triple in [i_lo, i_hi]
+        iteration(I0{}, Unchecked{}, zl0 + ib);
+        iteration(I1{}, Unchecked{}, zl0 + ib + 1);
+        iteration(I2{}, Unchecked{}, zl0 + ib + 2);
+    }
+    for (; ib < n_it; ib += 3) {
+        iteration(I0{}, Checked{}, zl0 + ib);
+        if (ib + 1 < n_it) iteration(I1{}, Checked{}, zl0 + ib + 1);
+        if (ib + 2 < n_it) iteration(I2{}, Checked{}, zl0 + ib + 2);
     }
     cp_async_wait<0>();
     __syncthreads();
