@@ -170,14 +170,11 @@ __device__ __forceinline__ int owner(const Proto* __restrict__ protos, int n, in
 // Arithmetic of one explicit substep, written with explicit round-to-nearest
 // intrinsics so that every kernel (scalar or packed f32x2) performs the same
 // operations in the same order and gets bit-identical FP32 results:
-//   s = ((((xm + xp) + ym) + yp) + zm) + zp;  lap = fma(-6, c, s);  t = fma(lam, lap, c)
+//   s = ((xm + xp) + (ym + yp)) + (zm + zp);  lap = fma(-6, c, s);  t = fma(lam, lap, c)
+// (a pairwise sum: three dependent additions instead of five)
 __device__ __forceinline__ float stencil_t(float c, float xm, float xp, float ym, float yp, float zm, float zp,
                                            float lam) {
-    float s = __fadd_rn(xm, xp);
-    s = __fadd_rn(s, ym);
-    s = __fadd_rn(s, yp);
-    s = __fadd_rn(s, zm);
-    s = __fadd_rn(s, zp);
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
     const float lap = __fmaf_rn(-6.f, c, s);
     return __fmaf_rn(lam, lap, c);
 }

@@ -63,11 +63,7 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // the pinned substep sequence of stencil_t on a column pair
 __device__ __forceinline__ float2 stencil_t2(float2 c, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm,
                                              float2 zp, float lam) {
-    float2 s = __fadd2_rn(xm, xp);
-    s = __fadd2_rn(s, ym);
-    s = __fadd2_rn(s, yp);
-    s = __fadd2_rn(s, zm);
-    s = __fadd2_rn(s, zp);
+    const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(ym, yp)), __fadd2_rn(zm, zp));
     const float2 lap = __ffma2_rn(f2(-6.f, -6.f), c, s);
     return __ffma2_rn(f2(lam, lam), lap, c);
 }
@@ -75,11 +71,7 @@ __device__ __forceinline__ float2 stencil_t2(float2 c, float2 xm, float2 xp, flo
 // the same sequence on two fields of one site (O2 and glucose), each with its own lambda
 __device__ __forceinline__ float2 stencil_t2l(float2 c, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm,
                                               float2 zp, float2 lam) {
-    float2 s = __fadd2_rn(xm, xp);
-    s = __fadd2_rn(s, ym);
-    s = __fadd2_rn(s, yp);
-    s = __fadd2_rn(s, zm);
-    s = __fadd2_rn(s, zp);
+    const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(ym, yp)), __fadd2_rn(zm, zp));
     const float2 lap = __ffma2_rn(f2(-6.f, -6.f), c, s);
     return __ffma2_rn(lam, lap, c);
 }
