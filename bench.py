@@ -155,10 +155,10 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel, n_protocols):
-    """DRAM bytes per launch from the committed ncu summary (per 64^3 protocol,
-    scaled to the batch), or None when the kernel source changed since the
-    counters were taken."""
+def traffic_for(kernel, n_sites):
+    """DRAM bytes per launch from the committed ncu capture (64 protocols of
+    64^3; bytes per site scaled to the batch's sites), or None when a kernel
+    source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -166,7 +166,7 @@ def traffic_for(kernel, n_protocols):
         d["sources"]
     except Exception:
         return None
-    return d["dram_bytes_per_protocol"] * n_protocols if sources_sha(d["sources"]) == d["source_sha"] else None
+    return d["dram_bytes_per_site"] * n_sites if sources_sha(d["sources"]) == d["source_sha"] else None
 
 
 def sources_sha(names):
@@ -298,7 +298,8 @@ def run_ours(args):
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
-            "traffic": traffic_for(traffic_key[name], N_PROT),
+            "traffic": traffic_for(traffic_key[name], sites),
+            "traffic_source": "ncu capture on 64 x 64^3 (profiles/traffic.json), scaled by sites",
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
             "kernel_share": {k: float(v / kms.sum()) for k, v in
                              zip(("reaction-diffusion", "cell-update pass", "claim", "resolve"), kms)}}

@@ -142,3 +142,35 @@ def evolve_on_device(sim, dga: DeviceGA, generations: int, seed: int, unit_gy: f
             break
         pop, spare = dga.generation(pop, fit, seed, g + 1, out=spare)[0], pop
     return pop, hist
+
+
+def main():
+    """Time one device GA generation at the paper-scale population (4,096 dose
+    vectors of 240 half-hour slots) for each selection scheme; one JSON line each."""
+    import json
+
+    import torch
+
+    P = 4096
+    for sel in ("simple", "roulette", "tournament"):
+        prm = make_params(n_slots=240, d_max=8, total_cap=40, min_gap=12, n_elite=410, n_parents=1638,
+                          selection=SEL[sel], crossover=CROSS["two_point"], mutations=15, p_mut=0.3)
+        dga = DeviceGA(prm, P)
+        pop = dga.random_population(7)
+        fit = torch.rand(P, device=pop.device)
+        out = torch.empty_like(pop)
+        for _ in range(3):
+            dga.generation(pop, fit, 7, 1, out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(dga.stream)
+        n = 20
+        for g in range(n):
+            dga.generation(pop, fit, 7, g, out=out)
+        b.record(dga.stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"selection": sel, "population": P, "slots": 240,
+                          "ms_per_generation": a.elapsed_time(b) / n}))
+
+
+if __name__ == "__main__":
+    main()
