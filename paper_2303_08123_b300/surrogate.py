@@ -119,13 +119,15 @@ class Surrogate:
             out[s:s + m] = self.forward(chunk).cpu().numpy()[:m]
         return out
 
-    def train_step(self, X, t, lr: float) -> float:
+    def train_step(self, X, t, lr: float, want_loss: bool = True):
+        """One Adam step; returns the loss before the step (synchronises), or None
+        without synchronising when want_loss is False."""
         Xd = X if hasattr(X, "data_ptr") else self._dev(X)
         td = t if hasattr(t, "data_ptr") else self._dev(t)
         loss = ctypes.c_float()
         _check(self._lib.mlp_train_step(self._ctx, Xd.data_ptr(), td.data_ptr(), Xd.shape[0], float(lr),
-                                        ctypes.byref(loss)))
-        return loss.value
+                                        ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
 
     def gradients(self, X, t):
         import torch
@@ -144,3 +146,36 @@ class Surrogate:
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
         _check(self._lib.mlp_set_params(self._ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+
+def main():
+    """Time the network on the tensor cores at the largest batch: forward and
+    one training step (forward, backward, Adam) over 4,096 rows; one JSON line."""
+    import json
+
+    import torch
+
+    B, n = 4096, 50
+    net = Surrogate(batch_max=B, seed=1)
+    X = torch.rand(B, 45, device=net.device)
+    t = torch.rand(B, device=net.device)
+    fwd_flop = 2.0 * B * (48 * 256 + 2 * 256 * 256 + 256)
+    out = {"batch": B}
+    for name, fn, flop in (("forward", lambda: net.forward(X), fwd_flop),
+                           ("train_step", lambda: net.train_step(X, t, 1e-4, want_loss=False), 3 * fwd_flop)):
+        for _ in range(5):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(net.stream)
+        for _ in range(n):
+            fn()
+        b.record(net.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        out[name] = {"ms": ms, "gemm_tflops": flop / (ms / 1e3) / 1e12}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
+
