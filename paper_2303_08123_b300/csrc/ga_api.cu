@@ -1,4 +1,6 @@
 // ga_api.cu -- extern "C" entry points of libga (include/ga.h).
+#include <atomic>
+
 #include "ga.h"
 #include "ga_kernels.cuh"
 
@@ -70,16 +72,18 @@ int row_threads(int S, int rows) {
     return 32;
 }
 
+// dynamic shared memory above 48 KB must be allowed once per device
 cudaError_t set_smem_attrs() {
-    static cudaError_t done = [] {
-        cudaError_t e = cudaFuncSetAttribute(gadev::k_children, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemBudget);
-        if (!e)
-            e = cudaFuncSetAttribute(gadev::k_random_population, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static std::atomic<uint64_t> done{0};  // bit d: device d is set up (devices 0..63; others every call)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 64 && ((done.load() >> dev) & 1u)) return cudaSuccess;
+    e = cudaFuncSetAttribute(gadev::k_children, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    if (!e) e = cudaFuncSetAttribute(gadev::k_random_population, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kSmemBudget);
-        return e;
-    }();
-    return done;
+    if (!e && dev < 64) done.fetch_or(1ull << dev);
+    return e;
 }
 
 int status_of(cudaError_t e) { return e == cudaSuccess ? 0 : -3; }
