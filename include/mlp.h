@@ -1,6 +1,6 @@
 /*
  * mlp.h -- C ABI of the surrogate network (libmlp) that pre-screens GA
- * candidates before the full simulator judges them.
+ * candidates before the full simulator evaluates them.
  *
  * The paper evaluates every candidate with the simulator ("The Main GA Loop",
  * Eq. final_fit_fun); this library adds a learned pre-screen on top of that

@@ -1,8 +1,8 @@
 """Surrogate-screened GA: the network ranks a large pool of candidate protocols,
-the full batched simulator judges the ones it promotes.
+the full batched simulator evaluates the ones it promotes.
 
 The paper's GA scores every candidate with the simulator ("The Main GA Loop");
-here the simulator stays the judge of every protocol that enters the
+here the simulator still scores every protocol that enters the
 population, and the surrogate (trained on the simulator's own output) only
 decides which candidates are worth simulating.
 

@@ -2,7 +2,7 @@
 
 The surrogate is trained on 2,048 simulated protocols.  From a fresh pool of
 4,096 candidates it promotes the 256 it predicts best; the same number of
-candidates drawn at random is the method without it.  Both sets are judged by
+candidates drawn at random is the method without it.  Both sets are scored by
 the full simulator: the promoted set must contain clearly better protocols
 (lower final live counts, a t-test far beyond chance), so the same search
 quality needs far fewer full simulations.  Its predictions must also rank a
