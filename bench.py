@@ -392,7 +392,11 @@ def full_run(args, sim, prot, mean_h, Ls, shape, shape_ms, world, rank, dev, bar
                                protocols_per_s="protocols / wall time of the whole batch (measured, not extrapolated)",
                                max_horizon_h=float(horizons.max())),
                 "site_updates_per_s": world * site_steps / (ms / 1e3),
-                "final_count_mean": float(np.mean(cnt)), "clocks": clk.summary()}
+                "final_count_mean": float(np.mean(cnt)),
+                # every CA step: the fused passes, claim, resolve; every hour: clock tick and count; then fitness
+                "gpu_launches": int(STEPS_PER_HOUR * horizons.max() * ((PARAMS.n_sub + 1) // 2 + 2)
+                                    + 2 * int(np.ceil(horizons.max())) + 1),
+                "clocks": clk.summary()}
         print(json.dumps(line))
     sim.close()
     return 0
