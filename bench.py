@@ -394,7 +394,8 @@ def full_run(args, sim, prot, mean_h, Ls, shape, shape_ms, world, rank, dev, bar
                 "site_updates_per_s": world * site_steps / (ms / 1e3),
                 "final_count_mean": float(np.mean(cnt)),
                 # every CA step: the fused passes, claim, resolve; every hour: clock tick and count; then fitness
-                "gpu_launches": int(STEPS_PER_HOUR * horizons.max() * ((PARAMS.n_sub + 1) // 2 + 2)
+                "gpu_launches": int(STEPS_PER_HOUR * horizons.max() * (((PARAMS.n_sub + 1) // 2 + 2)
+                                                                       if args.path == "fused" else PARAMS.n_sub + 3)
                                     + 2 * int(np.ceil(horizons.max())) + 1),
                 "clocks": clk.summary()}
         print(json.dumps(line))
