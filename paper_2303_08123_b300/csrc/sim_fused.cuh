@@ -436,9 +436,13 @@ constexpr size_t fused1_smem_bytes() {
 #ifndef SIM_FUSED1_MIN_BLOCKS_SMALL
 #define SIM_FUSED1_MIN_BLOCKS_SMALL 2  // CTAs per SM the 16 x 16 column kernel is register-budgeted for
 #endif
+#ifndef SIM_FUSED1_MIN_BLOCKS_LARGE
+#define SIM_FUSED1_MIN_BLOCKS_LARGE 1  // the same for the 32 x 16 column kernel
+#endif
 
 template <int TX, int TY, int K, bool EPI>
-__global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS, (TX * TY <= 256) ? SIM_FUSED1_MIN_BLOCKS_SMALL : 1)
+__global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
+                                  (TX * TY <= 256) ? SIM_FUSED1_MIN_BLOCKS_SMALL : SIM_FUSED1_MIN_BLOCKS_LARGE)
     k_fused1(const Tile* __restrict__ tiles, const Proto* __restrict__ protos, const int64_t* __restrict__ clock,
              int k_off, int first, const float* __restrict__ iO, const float* __restrict__ iG,
              const float* __restrict__ iH, float* __restrict__ oO, float* __restrict__ oG, float* __restrict__ oH,
