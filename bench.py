@@ -206,13 +206,15 @@ def run_reference(args):
     vals = []
     for _ in range(args.warmup):
         cpu_baseline(mean_h, max_steps=20)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
         vals.append(cpu_baseline(mean_h, max_steps=40))
+    ms_per_step = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
     v = statistics.mean(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(mean_h), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
