@@ -46,8 +46,16 @@ WORKLOAD = "ga_batch"
 PARAMS, PARAMS_NOTE = P0, ""
 
 
+def t_end_steps():
+    """Fixed horizon of the workload in steps (0: last fraction + 120 h per protocol)."""
+    return 288 * STEPS_PER_HOUR if WORKLOAD == "single" else 0
+
+
 def workload():
     """(protocols, mean horizon in h, lattice sides, radii) of the benchmarked batch."""
+    if WORKLOAD == "single":
+        prot = [workloads.daily_fractions(10, 2.0, 24.0)]
+        return prot, 288.0, np.array([40], dtype=np.int32), np.array([5], dtype=np.int32)
     if WORKLOAD == "ragged":
         Ls, Rs, prot = workloads.ragged_batch(N_PROT, seed=3)
     else:
@@ -58,6 +66,17 @@ def workload():
 
 
 def workload_config(mean_t_end_h, precision="fp32"):
+    if WORKLOAD == "single":
+        return {
+            "workload": "single protocol, 40^3 lattice, seeded spheroid R=5 (515 cells), 10 x 2 Gy at 24 h "
+                        f"intervals, fixed 288 h horizon (12 days), {precision} fields, n_sub={PARAMS.n_sub}"
+                        + PARAMS_NOTE,
+            "step": "one simulated hour (600 CA steps)",
+            "protocols_per_s": "1 / (seconds per simulated hour x 288 h)",
+            "mean_horizon_h": 288.0,
+            "l2": "L2-resident (fields 1.5 MB): latency-bound; the HBM fraction is a reference, not a DRAM figure",
+            "parallelism": "one protocol",
+        }
     if WORKLOAD == "ragged":
         _, _, Ls, _ = workload()
         return {
@@ -184,7 +203,7 @@ def cpu_baseline(mean_t_end_h, max_steps=None):
     cores = os.cpu_count() or 1
     prot, _, Ls, Rs = workload()
     n = min(cores, N_PROT)
-    steps = max_steps or (1200 if WORKLOAD != "ragged" else 300)
+    steps = max_steps or {"ragged": 300, "single": 6000}.get(WORKLOAD, 1200)
     off, d, w = _csr(prot[:n])
     t0 = time.perf_counter()
     res = oracle.run_batch(PARAMS, Ls[:n], Rs[:n], SEED, off, d, w, max_steps=steps, n_threads=n)
@@ -247,7 +266,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sim = Simulator(Ls, Rs, seed=SEED, precision=args.precision, hours=hours, params=PARAMS,
-                    dose_cap_gy=30.0, device=dev, path=args.path, tile_shape=args.tile_shape)
+                    dose_cap_gy=30.0, device=dev, path=args.path, tile_shape=args.tile_shape,
+                    t_end_steps=t_end_steps())
     sim.load_protocols(off, d, w)
     if args.path == "fused" and args.tile_shape == 0:
         shape, shape_ms = sim.autotune(10)  # re-seeds the batch at step 0
@@ -326,7 +346,7 @@ def run_ours(args):
 
     # plain form: one protocol at a time, per-step launches, no graph
     plain = Simulator(Ls[:1], Rs[:1], seed=SEED, precision=args.precision, use_graphs=False, dose_cap_gy=30.0,
-                      device=dev, path=args.path, params=PARAMS)
+                      device=dev, path=args.path, params=PARAMS, t_end_steps=t_end_steps())
     po, pd, pw = csr(prot[:1])
     plain.load_protocols(po, pd, pw)
     plain.run(50)
@@ -369,7 +389,7 @@ def full_run(args, sim, prot, mean_h, Ls, shape, shape_ms, world, rank, dev, bar
     import torch
     from paper_2303_08123_b300 import csr
     stream = torch.cuda.current_stream(dev)
-    horizons = np.array([sum(w) + 120.0 for _, w in prot])
+    horizons = np.array([t_end_steps() / STEPS_PER_HOUR if t_end_steps() else sum(w) + 120.0 for _, w in prot])
     barrier()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
@@ -415,8 +435,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "substep"])
     ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-4 (0: autotune)")
-    ap.add_argument("--workload", default="ga_batch", choices=["ga_batch", "ragged"],
-                    help="ga_batch: 256 x 64^3 (default); ragged: 1,024 protocols on 32^3-112^3")
+    ap.add_argument("--workload", default="ga_batch", choices=["ga_batch", "ragged", "single"],
+                    help="ga_batch: 256 x 64^3 (default); ragged: 1,024 protocols on 32^3-112^3; "
+                         "single: one protocol on 40^3 for 288 h")
     ap.add_argument("--protocols", type=int, default=256, help="batch size per GPU (smaller: profiling cases)")
     ap.add_argument("--params", default="p0", choices=["p0", "phys"],
                     help="p0: coarse-grained diffusion (4 substeps per step); phys: physical-rate variant "
@@ -429,6 +450,8 @@ def main():
     if args.params == "phys":
         PARAMS, PARAMS_NOTE = P_PHYS, " (physical-rate diffusion variant, uptake per substep scaled by 4/128)"
     N_PROT = args.protocols if not (args.workload == "ragged" and args.protocols == 256) else 1024
+    if args.workload == "single":
+        N_PROT = 1
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -403,3 +403,33 @@ def test_physical_rate_variant(cuda, orc):
         assert np.array_equal(cell, ref["state"].cell), (p, ref["stats"])
         for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
             assert np.max(np.abs(g - o)) / m < 1e-4
+
+
+def test_single_protocol_configuration(cuda, orc):
+    """The single-protocol case (40^3, R = 5, 10 x 2 Gy at 24 h intervals, 12
+    days): the whole 288 h run on the fused hour-graph path equals the substep
+    path (all 289 hourly counts and the final state, bit for bit), and its first
+    26 hours (two fractions) equal the oracle (hourly counts and cells)."""
+    from paper_2303_08123_b300 import csr
+    from synth import workloads
+    doses, waits = workloads.daily_fractions(10, 2.0, 24.0)
+    T = 288 * 600
+    out = []
+    for path in ("fused", "substep"):
+        sim = _sim([40], [5], hours=288, t_end_steps=T, path=path)
+        sim.load_protocols(*csr([(doses, waits)]))
+        sim.run(0)
+        out.append((sim.counts()[0], sim.get_state(0)))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    for x, y in zip(out[0][1], out[1][1]):
+        assert np.array_equal(x, y)
+    assert out[0][0][0] == 515 and np.all(out[0][0] > 0)
+    Ts = 26 * 600
+    sim = _sim([40], [5], hours=26, t_end_steps=Ts)
+    sim.load_protocols(*csr([(doses, waits)]))
+    sim.run(0)
+    ref = orc.run(P0, 40, 5, SEED, 0, doses, waits, t_end_steps=Ts, hours=26)
+    assert np.array_equal(sim.counts()[0], ref["counts"])
+    assert np.array_equal(sim.get_state(0)[3], ref["state"].cell), ref["stats"]
+    assert np.array_equal(sim.counts()[0], out[0][0][:27])
