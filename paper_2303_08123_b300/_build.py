@@ -18,11 +18,13 @@ LIBDIR = os.path.join(PKG, "_lib")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
-# one shared library per entry translation unit
+# one shared library per entry translation unit: (sources, extra nvcc flags)
 TARGETS = {
-    "libsim.so": ["sim_api.cu"],
-    "libmlp.so": ["mlp_api.cu"],
-    "libga.so": ["ga_api.cu"],
+    "libsim.so": (["sim_api.cu"], []),
+    "libmlp.so": (["mlp_api.cu"], []),
+    "libga.so": (["ga_api.cu"], []),
+    # debug variant of libsim: every kernel's site indices checked, violations reported in the status word
+    "libsim_check.so": (["sim_api.cu"], ["-DSIM_CHECK"]),
 }
 
 
@@ -35,14 +37,14 @@ def build(force: bool = False, verbose: bool = False) -> list:
     os.makedirs(LIBDIR, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _deps())
     out = []
-    for lib, srcs in TARGETS.items():
+    for lib, (srcs, flags) in TARGETS.items():
         dst = os.path.join(LIBDIR, lib)
         out.append(dst)
         if not force and os.path.exists(dst) and os.path.getmtime(dst) >= newest:
             continue
         tmp = dst + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-               "-cudart", "shared", "-I", os.path.join(ROOT, "include"), "-o", tmp,
+               "-cudart", "shared", "-I", os.path.join(ROOT, "include"), *flags, "-o", tmp,
                *[os.path.join(CSRC, s) for s in srcs]]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")

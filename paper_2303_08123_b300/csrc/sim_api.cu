@@ -400,7 +400,7 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, in
         k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                           c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
                                           c->at<unsigned long long>(c->lay.claim), c->at<uint32_t>(c->lay.tile_ctr),
-                                          c->passes(), kMaxPasses);
+                                          c->passes(), kMaxPasses, c->P);
         if (ev) cudaEventRecord(ev[4], s);
         return cuda_check(c, cudaGetLastError(), "step launch");
     }
@@ -426,7 +426,7 @@ sim_status enqueue_step(sim_ctx* c, cudaStream_t s, int k_off, int start_buf, in
     if (ev) cudaEventRecord(ev[3], s);
     k_resolve<<<ng, kThreads, 0, s>>>(protos, c->n, clock, k_off, cell, c->at<uint32_t>(c->lay.intents),
                                       c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.target),
-                                      c->at<unsigned long long>(c->lay.claim), nullptr, 0, kMaxPasses);
+                                      c->at<unsigned long long>(c->lay.claim), nullptr, 0, kMaxPasses, c->P);
     if (ev) cudaEventRecord(ev[4], s);
     return cuda_check(c, cudaGetLastError(), "step launch");
 }
@@ -512,6 +512,8 @@ sim_status read_status(sim_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(&st, c->ws + c->lay.status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_check(c, e, "synchronise");
+    if (st & kStatusBounds)
+        return fail(c, SIM_ECUDA, "index check failed: a kernel addressed a site outside the batch (SIM_CHECK build)");
     if (st & kStatusBadProtocol)
         return fail(c, SIM_EINVAL,
                     "a protocol loaded from device dose vectors exceeds max_fractions or the dose cap "
@@ -679,6 +681,8 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
         nt = t > nt ? t : nt;
     }
     c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size(), nt);
+    c->P.n_sites = (uint64_t)site0;
+    c->P.status = c->at<uint32_t>(c->lay.status);
     std::vector<int32_t> first_block(n + 1, 0);
     for (size_t b = 0; b < c->blocks.size(); ++b) first_block[c->blocks[b].p + 1] = (int32_t)(b + 1);
     cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.blocks, c->blocks.data(), sizeof(Block) * c->blocks.size(),
@@ -1236,8 +1240,9 @@ extern "C" sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t 
         base = g_noalloc_base[dev];
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const Params P = make_params(*cfg);
+    Params P = make_params(*cfg);  // frac_cap 0: the one fraction is its own quadratic partner
     const int64_t sites = (int64_t)L * L * L;
+    P.n_sites = (uint64_t)sites;  // no status word here: index checks of a SIM_CHECK build skip silently
     Proto pr{};
     pr.L = L;
     pr.R = -1;

@@ -38,7 +38,26 @@ struct Params {
     float O_q, G_q, H_q, G_d, H_d;
     uint32_t key0, key1, init_word;
     int frac_cap;  // fraction-table entries per array: doses at [0, cap), quadratic partners at [cap, 2 cap)
+    uint64_t n_sites;  // sites of the batch (index checks of the SIM_CHECK build)
+    uint32_t* status;  // the context's device status word (may be null)
 };
+
+// Device status bits (read back by every synchronising call).
+constexpr uint32_t kStatusBadProtocol = 2u;  // a protocol loaded on the device broke a limit
+constexpr uint32_t kStatusBounds = 4u;       // SIM_CHECK build: an index fell outside the batch
+
+// Debug build (-DSIM_CHECK): every global site index of the kernels is checked
+// against the batch; a violation sets kStatusBounds and the access is skipped
+// (nothing traps).  Compiled out otherwise.
+#ifdef SIM_CHECK
+__device__ __forceinline__ bool site_ok(const Params& P, int64_t idx) {
+    if ((uint64_t)idx < P.n_sites) return true;
+    if (P.status) atomicOr(P.status, kStatusBounds);
+    return false;
+}
+#else
+__device__ __forceinline__ bool site_ok(const Params&, int64_t) { return true; }
+#endif
 
 struct Proto {
     int32_t L;

@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
 
     // queue the copies of level-0 plane j into its stage (one commit group per plane, even when empty)
     auto prefetch = [&](int j) {
-        if (act && j <= zl1) {
+        if (act && j <= zl1 && (!ina || site_ok(P, pr.site0 + col + (int64_t)j * LL)) &&
+            (!inb || site_ok(P, pr.site0 + col + (int64_t)j * LL + 1))) {  // site checks: SIM_CHECK build only
             const int s = (j - zl0) % kStages;
             const int o = j * LL;
             T* sf = stage_f + (size_t)s * 3 * NC + sidx;
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
                 const bool oa = outa && oz, ob = outb && oz;
                 bool wa = false, wb = false;
                 const int o = q * LL;
-                if (oa || ob) {
+                if ((oa || ob) && (!oa || site_ok(P, pr.site0 + col + o)) && (!ob || site_ok(P, pr.site0 + col + o + 1))) {
                     const bool zface = q == 0 || q == L - 1;
                     const bool sa = oa && !fa && !zface, sb = ob && !fb && !zface;  // interior sites written
                     const bool vw = vec && sa && sb;
@@ -394,8 +395,9 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
                         slot = __shfl_sync(0xffffffffu, slot, leader);
                         const uint32_t lt = (1u << lane) - 1u;
                         const uint32_t g = (uint32_t)(pr.site0 + col + o);
-                        if (wa) intents[slot + __popc(ma & lt)] = g;
-                        if (wb) intents[slot + __popc(ma) + __popc(mb & lt)] = g + 1;
+                        const uint32_t ata = slot + __popc(ma & lt), atb = slot + __popc(ma) + __popc(mb & lt);
+                        if (wa && site_ok(P, ata)) intents[ata] = g;
+                        if (wb && site_ok(P, atb)) intents[atb] = g + 1;
                     }
                 }
             }
@@ -514,10 +516,12 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
             const int s = (j - zl0) & (kS1 - 1);
             const int o = j * LL;
             float2* sog = my_og + s * NC;
-            cp_async(&sog->x, g0 + o, 4, in);
-            cp_async(&sog->y, g1 + o, 4, in);
-            cp_async(my_h + s * NC, g2 + o, 4, in);
-            cp_async(my_cell + s * NC, gC + o, 4, in);
+            if (site_ok(P, pr.site0 + col + o)) {  // SIM_CHECK build only
+                cp_async(&sog->x, g0 + o, 4, in);
+                cp_async(&sog->y, g1 + o, 4, in);
+                cp_async(my_h + s * NC, g2 + o, 4, in);
+                cp_async(my_cell + s * NC, gC + o, 4, in);
+            }
         }
         cp_async_commit();
     };
@@ -625,7 +629,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
             } else {
                 bool want = false;
                 const int o = q * LL;
-                if (outc && (!CHK || (q >= z0 && q < z1))) {
+                if (outc && (!CHK || (q >= z0 && q < z1)) && site_ok(P, pr.site0 + col + o)) {
                     const bool face = fxy || (CHK && (q == 0 || q == L - 1));
                     const int64_t g = pr.site0 + col + o;
                     if (!face) {
@@ -645,7 +649,8 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                         uint32_t slot = 0;
                         if (lane == leader) slot = atomicAdd(cnt, (uint32_t)__popc(mask));
                         slot = __shfl_sync(0xffffffffu, slot, leader);
-                        if (want) intents[slot + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(pr.site0 + col + o);
+                        const uint32_t at = slot + __popc(mask & ((1u << lane) - 1u));
+                        if (want && site_ok(P, at)) intents[at] = (uint32_t)(pr.site0 + col + o);
                     }
                 }
             }

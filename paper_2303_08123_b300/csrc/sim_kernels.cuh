@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
         const int x = (int)(s % L), y = (int)((s / L) % L), z = (int)(s / LL);
         if (is_face(L, x, y, z)) continue;
         const int64_t g = pr.site0 + s;
+        if (!site_ok(P, g - LL) || !site_ok(P, g + LL)) continue;  // SIM_CHECK build only
         const float O = ld(iO + g), Gv = ld(iG + g), H = ld(iH + g);
         uint32_t w = cell[g];
         const uint32_t kind = w & kKindMask;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_cell(const Block* __restrict__ blo
         const int i = base + threadIdx.x;
         bool want = false;
         int64_t g = 0;
-        if (i < b.n) {
+        if (i < b.n && site_ok(P, pr.site0 + b.begin + i)) {
             g = pr.site0 + b.begin + i;
             const uint32_t w = cell[g];
             if ((w & kKindMask) != kEmpty) {
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(kThreads) k_cell(const Block* __restrict__ blo
             uint32_t slot = 0;
             if (lane == leader) slot = atomicAdd(cnt, (uint32_t)__popc(mask));
             slot = __shfl_sync(0xffffffffu, slot, leader);
-            if (want) intents[slot + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)g;
+            const uint32_t at = slot + __popc(mask & ((1u << lane) - 1u));
+            if (want && site_ok(P, at)) intents[at] = (uint32_t)g;
         }
     }
 }
@@ -190,6 +192,10 @@ __global__ void __launch_bounds__(kThreads) k_claim(const Proto* __restrict__ pr
     const uint32_t n = icount[step & 1];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int64_t g = intents[i];
+        if (!site_ok(P, g)) {
+            target[i] = 0xffffffffu;
+            continue;
+        }
         const int p = owner(protos, n_protos, g);
         const Proto pr = protos[p];
         const int L = pr.L;
@@ -210,7 +216,8 @@ __global__ void __launch_bounds__(kThreads) k_claim(const Proto* __restrict__ pr
                     if (dx == 0 && dy == 0 && dz == 0) continue;
                     const int xx = x + dx, yy = y + dy, zz = z + dz;
                     const int64_t t = g + dx + (int64_t)L * (dy + (int64_t)L * dz);
-                    if (!is_face(L, xx, yy, zz) && (cell[t] & kKindMask) == kEmpty) freebits |= 1u << j;
+                    if (!is_face(L, xx, yy, zz) && site_ok(P, t) && (cell[t] & kKindMask) == kEmpty)
+                        freebits |= 1u << j;
                     ++j;
                 }
         const uint32_t nf = __popc(freebits);
@@ -226,6 +233,10 @@ __global__ void __launch_bounds__(kThreads) k_claim(const Proto* __restrict__ pr
         const int q = (jj >= 13) ? jj + 1 : jj;  // its position in the 27-point cube (centre = 13)
         const int qz = q / 9 - 1, qy = (q / 3) % 3 - 1, qx = q % 3 - 1;
         const int64_t t = g + qx + (int64_t)L * (qy + (int64_t)L * qz);
+        if (!site_ok(P, t)) {
+            target[i] = 0xffffffffu;
+            continue;
+        }
         target[i] = (uint32_t)t;
         atomicMax(claim + t, ((unsigned long long)(uint32_t)step << 32) | (unsigned long long)(0xffffffffu - (uint32_t)s));
     }
@@ -240,7 +251,8 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const Proto* __restrict__ 
                                                       uint32_t* __restrict__ icount,
                                                       const uint32_t* __restrict__ target,
                                                       const unsigned long long* __restrict__ claim,
-                                                      uint32_t* __restrict__ tile_ctr, int n_pass, int slots) {
+                                                      uint32_t* __restrict__ tile_ctr, int n_pass, int slots,
+                                                      Params P) {
     const int64_t step = *clock + k_off;
     const uint32_t n = icount[step & 1];
     if (blockIdx.x == 0 && threadIdx.x == 0) icount[(step + 1) & 1] = 0;
@@ -251,6 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const Proto* __restrict__ 
         const uint32_t t = target[i];
         if (t == 0xffffffffu) continue;
         const int64_t g = intents[i];
+        if (!site_ok(P, g) || !site_ok(P, t)) continue;
         const int p = owner(protos, n_protos, g);
         const uint32_t s = (uint32_t)(g - protos[p].site0);
         const unsigned long long key = ((unsigned long long)(uint32_t)step << 32) | (unsigned long long)(0xffffffffu - s);
@@ -366,7 +379,6 @@ __global__ void k_totals_finish(const int32_t* __restrict__ first_block, int n, 
 // fills the quadratic LQ partner of each fraction (incomplete repair with
 // half-time half_h > 0, the dose itself otherwise).  A protocol that breaks a
 // limit gets no fractions and raises bit kStatusBadProtocol of *status.
-constexpr uint32_t kStatusBadProtocol = 2u;
 constexpr int kStepsPerSlot = 300;
 
 __global__ void k_load_vectors(const uint8_t* __restrict__ units, int S, double unit_gy, int n,

@@ -101,15 +101,19 @@ SIGNATURES = {
 }
 
 
-def library_path() -> str:
-    return os.path.join(_LIBDIR, "libsim.so")
+def library_path(check: bool = False) -> str:
+    return os.path.join(_LIBDIR, "libsim_check.so" if check else "libsim.so")
 
 
-def load_library() -> ctypes.CDLL:
-    """Load libsim.so; raises if it has not been built (no fallback exists)."""
-    global _lib
-    if _lib is None:
-        path = library_path()
+_check_lib = None
+
+
+def load_library(check: bool = False) -> ctypes.CDLL:
+    """Load libsim.so (check=True: the index-checking debug build libsim_check.so);
+    raises if it has not been built (no fallback exists)."""
+    global _lib, _check_lib
+    if (_check_lib if check else _lib) is None:
+        path = library_path(check)
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is missing: build it with `python -m paper_2303_08123_b300._build` "
                                "(the simulator has no CPU fallback)")
@@ -117,8 +121,11 @@ def load_library() -> ctypes.CDLL:
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)
             fn.restype, fn.argtypes = res, args
-        _lib = lib
-    return _lib
+        if check:
+            _check_lib = lib
+        else:
+            _lib = lib
+    return _check_lib if check else _lib
 
 
 def _ptr(a, ct):
@@ -152,13 +159,16 @@ class Simulator:
 
     L, R: lattice size and initial spheroid radius per slot.  The workspace is
     a PyTorch uint8 tensor on `device`; work runs on `stream` (default: the
-    current PyTorch stream).
+    current PyTorch stream).  check=True runs the index-checking debug build
+    (a kernel that addresses a site outside the batch skips the access and the
+    next synchronising call raises).
     """
 
-    def __init__(self, L, R, config: SimConfig | None = None, device="cuda", stream=None, **cfg_kw):
+    def __init__(self, L, R, config: SimConfig | None = None, device="cuda", stream=None, check: bool = False,
+                 **cfg_kw):
         import torch
 
-        self._lib = load_library()
+        self._lib = load_library(check)
         self.L = np.ascontiguousarray(L, dtype=np.int32)
         self.R = np.ascontiguousarray(R, dtype=np.int32)
         self.n = len(self.L)
