@@ -71,15 +71,28 @@ def fit_surrogate(net: Surrogate, X, y, epochs: int = 200, batch: int = 256, lr:
 
 
 def run_ga(setup: SimSetup, cfg: ga.GAConfig, generations: int, rng, net: Surrogate | None = None,
-           pool: int = 0, scaling=None):
+           pool: int = 0, scaling=None, log=None):
     """GA with elitism.  Without a surrogate every child is simulated; with one,
     `pool` children are generated per generation, the surrogate keeps the
     cfg.population - elites most promising (lowest predicted count) and only
-    those are simulated.  Returns per-generation best count and simulations used."""
+    those are simulated.  Returns per-generation best count and simulations used.
+    `log` (a writable text file, optional) receives one JSON line per generation:
+    best and mean final count, simulations so far, the best protocol."""
+    import json
+
+    def record(g, counts, pop, used):
+        if log is not None:
+            b = int(np.argmin(counts))
+            doses, waits = ga.to_pairs(pop[b])
+            log.write(json.dumps({"generation": g, "best_count": float(counts[b]), "mean_count": float(counts.mean()),
+                                  "simulations": used, "best_protocol": {"dose_gy": doses, "wait_h": waits}}) + "\n")
+            log.flush()
+
     pop = [ga.random_protocol(cfg, rng) for _ in range(cfg.population)]
     counts = simulate([ga.to_pairs(p) for p in pop], setup, seed_offset=0)
     used = len(pop)
     history = [(float(counts.min()), used)]
+    record(0, counts, pop, used)
     for g in range(1, generations + 1):
         elites, children = ga.next_generation(pop, -counts, cfg, rng,
                                               n_children=pool if net is not None else None)
@@ -91,6 +104,7 @@ def run_ga(setup: SimSetup, cfg: ga.GAConfig, generations: int, rng, net: Surrog
         counts = simulate([ga.to_pairs(p) for p in pop], setup, seed_offset=g)
         used += len(pop)
         history.append((float(counts.min()), used))
+        record(g, counts, pop, used)
     return history
 
 
@@ -106,6 +120,7 @@ def main():
     ap.add_argument("--population", type=int, default=128)
     ap.add_argument("--pool", type=int, default=2048)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--log", default="", help="directory for one JSONL file per arm (generation by generation)")
     a = ap.parse_args()
     setup = SimSetup(L=24, R=5, regrowth_h=6)
     cfg = ga.GAConfig(n_slots=48, d_max=2.5, total_cap=8.0, min_gap=4, population=a.population,
@@ -116,7 +131,10 @@ def main():
     net = Surrogate(batch_max=4096, seed=a.seed)
     fit_surrogate(net, features(train), y, epochs=60)
     for arm, kw in (("full simulation only", {}), ("surrogate-screened", {"net": net, "pool": a.pool})):
-        hist = run_ga(setup, cfg, a.generations, np.random.default_rng(a.seed + 1), **kw)
+        log = open(f"{a.log}/ga_{arm.split()[0].replace('-', '_')}.jsonl", "w") if a.log else None
+        hist = run_ga(setup, cfg, a.generations, np.random.default_rng(a.seed + 1), log=log, **kw)
+        if log:
+            log.close()
         extra = a.train if kw else 0
         print(json.dumps({"arm": arm, "best_count": [h[0] for h in hist],
                           "simulations": [h[1] + extra for h in hist], "training_simulations": extra}))
