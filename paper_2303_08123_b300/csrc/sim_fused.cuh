@@ -509,6 +509,10 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     const float* g1 = iG + pr.site0 + col;
     const float* g2 = iH + pr.site0 + col;
     const uint32_t* gC = cin + pr.site0 + col;
+    float* const d0 = oO + pr.site0 + col;  // this column's outputs: plane q at offset q * L^2
+    float* const d1 = oG + pr.site0 + col;
+    float* const d2 = oH + pr.site0 + col;
+    uint32_t* const dC = cout + pr.site0 + col;
     const bool fetch = act;  // every active thread copies (zero-filled outside the lattice)
 
     auto prefetch = [&](int j) {
@@ -631,17 +635,16 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                 const int o = q * LL;
                 if (outc && (!CHK || (q >= z0 && q < z1)) && site_ok(P, pr.site0 + col + o)) {
                     const bool face = fxy || (CHK && (q == 0 || q == L - 1));
-                    const int64_t g = pr.site0 + col + o;
                     if (!face) {
-                        oO[g] = vog.x;
-                        oG[g] = vog.y;
-                        oH[g] = vh;
+                        d0[o] = vog.x;
+                        d1[o] = vog.y;
+                        d2[o] = vh;
                     }
                     const uint32_t w0 = wr[sq];
-                    if (EPI) cout[g] = face ? w0 : update_cell(w0, vog.x, vog.y, vh, P, want);
-                    else if (hit >> sq & 1u) cout[g] = w0;
+                    if (EPI) dC[o] = face ? w0 : update_cell(w0, vog.x, vog.y, vh, P, want);
+                    else if (dose > 0.f && (hit >> sq & 1u)) dC[o] = w0;  // only irradiation changes words here
                 }
-                hit &= ~(1u << sq);
+                if (!EPI && dose > 0.f) hit &= ~(1u << sq);
                 if (EPI) {
                     const uint32_t mask = __ballot_sync(0xffffffffu, want);
                     if (mask) {
