@@ -81,7 +81,8 @@ typedef struct {
     int32_t path;           /* SIM_PATH_FUSED (default) or SIM_PATH_SUBSTEP */
     int32_t tile_shape;     /* fused tile: 0 auto; 1 = 32 x 16, 2 = 16 x 16 with two columns per
                                thread (packed FP32); 3 = 32 x 16, 4 = 16 x 16 with one column per
-                               thread (FP32 storage only) */
+                               thread.  For a given storage precision every shape gives the same
+                               results bit for bit */
     int32_t z_chunk;        /* fused z range per CTA: 0 auto, else planes per CTA */
 } sim_config;
 

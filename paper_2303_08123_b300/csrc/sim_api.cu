@@ -18,6 +18,7 @@
 #include "../../include/sim.h"
 #include "sim_kernels.cuh"
 #include "sim_fused.cuh"
+#include "sim_fused1h.cuh"
 
 using namespace simdev;
 
@@ -286,17 +287,30 @@ void launch_fused_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, c
         c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr), (int)c->tiles.size(), pass, c->P);
 }
 
-template <int TX, int TY, int K, bool EPI>
+// the one-column-per-thread kernel of storage type T: k_fused1 for FP32, k_fused1h for 2-byte types
+template <typename T, int TX, int TY, int K, bool EPI>
+constexpr auto fused1_kernel() {
+    if constexpr (std::is_same<T, float>::value) return k_fused1<TX, TY, K, EPI>;
+    else return k_fused1h<T, TX, TY, K, EPI>;
+}
+template <typename T, int TX, int TY, int K>
+constexpr size_t fused1_bytes() {
+    if constexpr (std::is_same<T, float>::value) return fused1_smem_bytes<TX, TY, K>();
+    else return fused1h_smem_bytes<T, TX, TY, K>();
+}
+
+template <typename T, int TX, int TY, int K, bool EPI>
 void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin,
                      uint32_t* cout, int pass) {
     using Sh = FusedShape1<TX, TY, K>;
+    constexpr auto kern = fused1_kernel<T, TX, TY, K, EPI>();
     static unsigned grid = 0;
-    if (!grid) grid = persistent_grid(k_fused1<TX, TY, K, EPI>, Sh::THREADS, fused1_smem_bytes<TX, TY, K>(), ~0ull);
+    if (!grid) grid = persistent_grid(kern, Sh::THREADS, fused1_bytes<T, TX, TY, K>(), ~0ull);
     const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
-    k_fused1<TX, TY, K, EPI><<<g, Sh::THREADS, fused1_smem_bytes<TX, TY, K>(), s>>>(
+    kern<<<g, Sh::THREADS, fused1_bytes<T, TX, TY, K>(), s>>>(
         c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first,
-        (const float*)c->field(buf, 0), (const float*)c->field(buf, 1), (const float*)c->field(buf, 2),
-        (float*)c->field(buf ^ 1, 0), (float*)c->field(buf ^ 1, 1), (float*)c->field(buf ^ 1, 2), cin, cout,
+        (const T*)c->field(buf, 0), (const T*)c->field(buf, 1), (const T*)c->field(buf, 2),
+        (T*)c->field(buf ^ 1, 0), (T*)c->field(buf ^ 1, 1), (T*)c->field(buf ^ 1, 2), cin, cout,
         c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
         c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr),
         (int)c->tiles.size(), pass, c->P);
@@ -305,10 +319,8 @@ void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, 
 template <typename T, int K, bool EPI>
 void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
                     int pass) {
-    if constexpr (std::is_same<T, float>::value) {
-        if (c->shape == 3) return launch_fused1_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
-        if (c->shape == 4) return launch_fused1_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
-    }
+    if (c->shape == 3) return launch_fused1_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+    if (c->shape == 4) return launch_fused1_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     if (c->shape == 2) launch_fused_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     else launch_fused_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
 }
@@ -330,19 +342,19 @@ cudaError_t fused_attrs_shape() {
     return e;
 }
 
-template <int TX, int TY>
+template <typename T, int TX, int TY>
 cudaError_t fused1_attrs_shape() {
-    cudaError_t e = cudaFuncSetAttribute(k_fused1<TX, TY, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fused1_smem_bytes<TX, TY, 1>());
+    cudaError_t e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 1, false>(),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused1_bytes<T, TX, TY, 1>());
     if (!e)
-        e = cudaFuncSetAttribute(k_fused1<TX, TY, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused1_smem_bytes<TX, TY, 1>());
+        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 1, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused1_bytes<T, TX, TY, 1>());
     if (!e)
-        e = cudaFuncSetAttribute(k_fused1<TX, TY, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused1_smem_bytes<TX, TY, 2>());
+        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 2, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused1_bytes<T, TX, TY, 2>());
     if (!e)
-        e = cudaFuncSetAttribute(k_fused1<TX, TY, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused1_smem_bytes<TX, TY, 2>());
+        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 2, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused1_bytes<T, TX, TY, 2>());
     return e;
 }
 
@@ -350,10 +362,8 @@ template <typename T>
 cudaError_t fused_attrs() {
     cudaError_t e = fused_attrs_shape<T, 32, 16>();
     if (!e) e = fused_attrs_shape<T, 16, 16>();
-    if constexpr (std::is_same<T, float>::value) {
-        if (!e) e = fused1_attrs_shape<32, 16>();
-        if (!e) e = fused1_attrs_shape<16, 16>();
-    }
+    if (!e) e = fused1_attrs_shape<T, 32, 16>();
+    if (!e) e = fused1_attrs_shape<T, 16, 16>();
     return e;
 }
 
@@ -911,7 +921,6 @@ sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     int pick = c->shape;
     sim_status st = SIM_OK;
     for (int sh = 1; sh <= kNumShapes && st == SIM_OK; ++sh) {
-        if (sh > 2 && c->cfg.precision != SIM_FP32) continue;
         st = set_shape(c, sh, L);
         // one untimed step (first touch), then n_steps timed plain steps
         for (int i = 0; i <= n_steps && st == SIM_OK; ++i) {

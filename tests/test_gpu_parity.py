@@ -433,3 +433,25 @@ def test_single_protocol_configuration(cuda, orc):
     assert np.array_equal(sim.counts()[0], ref["counts"])
     assert np.array_equal(sim.get_state(0)[3], ref["state"].cell), ref["stats"]
     assert np.array_equal(sim.counts()[0], out[0][0][:27])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_two_byte_storage_same_on_every_tile_shape(cuda, precision):
+    """BF16 / FP16 storage: the one-column kernels (shapes 3, 4) stage element
+    pairs and round with the same counter-based bits as the column-pair kernels
+    (shapes 1, 2), so every shape gives the same fields and cells bit for bit
+    (1,500 steps with a fraction, lattices 16-48, a z split)."""
+    from paper_2303_08123_b300 import csr
+    L, R = [16, 32, 48, 32], [3, 5, 7, 4]
+    prot = [([2.0], [0.5]), ([1.0, 2.0], [0.5, 1.0]), ([3.0], [1.0]), ([], [])]
+    out = []
+    for shape, zc in ((1, 0), (2, 0), (3, 0), (4, 0), (4, 12)):
+        sim = _sim(L, R, hours=2, t_end_steps=1500, precision=precision, tile_shape=shape, z_chunk=zc)
+        sim.load_protocols(*csr(prot))
+        sim.run(0)
+        out.append([sim.get_state(p) for p in range(len(L))])
+        sim.close()
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
