@@ -304,7 +304,7 @@ def run_ours(args):
     interior = float(np.sum((Ls.astype(np.float64) - 2) ** 3))
     es = 4 if args.precision == "fp32" else 2
     if args.path == "fused":
-        kn = "k_fused1" if shape in (3, 4) else "k_fused"  # shape 0 only on the substep path
+        kn = ("k_fused1" if args.precision == "fp32" else "k_fused1h") if shape in (3, 4) else "k_fused"
         classes = {f"{kn} (first pass: irradiation + 2 substeps)": (kms[0], kl[0], interior * (6 * es + 4)),
                    f"{kn} (last pass: 2 substeps + cell update)": (kms[1], kl[1], interior * (6 * es + 8))}
         traffic_key = {f"{kn} (first pass: irradiation + 2 substeps)": f"{kn}_first_shape{shape}",

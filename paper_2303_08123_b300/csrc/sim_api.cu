@@ -94,7 +94,6 @@ bool valid_config(const sim_config* cfg, std::string* why) {
     if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
     if (cfg->path < SIM_PATH_FUSED || cfg->path > SIM_PATH_SUBSTEP) return *why = "unknown kernel path", false;
     if (cfg->tile_shape < 0 || cfg->tile_shape > 4) return *why = "tile_shape must be in 0..4", false;
-    if (cfg->tile_shape > 2 && cfg->precision != SIM_FP32) return *why = "column-per-thread shapes need FP32", false;
     if (cfg->z_chunk < 0) return *why = "z_chunk must be >= 0", false;
     return true;
 }
