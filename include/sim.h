@@ -19,6 +19,12 @@
  *  - Work is enqueued on the CUDA stream given to sim_create.  Calls marked
  *    "synchronises" wait for that stream and report device-side errors.
  *  - A context is not thread-safe; use one context per host thread.
+ *  - Conditions found on the device are recorded in the context's status word
+ *    and returned by the next synchronising call: a protocol loaded from device
+ *    dose vectors that breaks a limit (SIM_EINVAL) and, in the index-checking
+ *    debug build of this library (libsim_check.so, compiled with SIM_CHECK), a
+ *    kernel addressing a site outside the batch (SIM_ECUDA; the access is
+ *    skipped).  sim_reset and the protocol loaders clear the word.
  *  - Lattice site index s = x + L*(y + L*z); sites with a coordinate equal to
  *    0 or L-1 are faces that hold the medium values and never hold cells.
  *  - Cell word: bits 0..2 kind (0 empty, 1 G1, 2 S, 3 G2, 4 M, 5 quiescent),
