@@ -104,21 +104,22 @@ constexpr int kNumShapes = 4;
 constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0}, {32, 16}, {16, 16}, {32, 16}, {16, 16}};
 constexpr int kTargetCtas = 2 * 148;  // at least two CTAs per SM when the batch allows it
 
-// Tile shape: the one covering the fewest sites (ties: the larger tile).
+// Default tile shape (the autotuner may pick any): one column per thread, the
+// tile covering the fewest sites; on a tie the larger tile, unless the batch
+// then has too few tiles to give every SM two CTAs' worth of work.
 int pick_shape(const sim_config& cfg, int n, const int32_t* L) {
     if (cfg.tile_shape) return cfg.tile_shape;
-    int64_t best = -1;
-    int pick = 1;
-    for (int sh = 1; sh <= 2; ++sh) {  // default: packed shapes; the autotuner may pick any
-        int64_t area = 0;
+    int64_t area[kNumShapes + 1] = {}, tiles[kNumShapes + 1] = {};
+    for (int sh = 3; sh <= 4; ++sh)
         for (int p = 0; p < n; ++p) {
             const int64_t tx = (L[p] + kTileShapes[sh][0] - 1) / kTileShapes[sh][0];
             const int64_t ty = (L[p] + kTileShapes[sh][1] - 1) / kTileShapes[sh][1];
-            area += tx * kTileShapes[sh][0] * ty * kTileShapes[sh][1] * (int64_t)L[p];
+            area[sh] += tx * kTileShapes[sh][0] * ty * kTileShapes[sh][1] * (int64_t)L[p];
+            tiles[sh] += tx * ty;
         }
-        if (best < 0 || area < best) best = area, pick = sh;
-    }
-    return pick;
+    if (area[4] < area[3]) return 4;
+    if (area[3] < area[4]) return 3;
+    return tiles[3] >= kTargetCtas ? 3 : 4;
 }
 
 // Fused work list: column tiles of every protocol still running (live[p] != 0;
