@@ -178,3 +178,43 @@ def test_guards_on_hand_cases():
     v = [9, 0, 0, 0]
     oga.repair(v, oga.GAParams(n_slots=4, d_max=8, total_cap=99, min_gap=1), d)
     assert v == [8, 0, 0, 0]
+
+
+@pytest.mark.parametrize("cross", [oga.X_SINGLE, oga.X_TWO])
+def test_crossover_cut_points_cover_exactly_the_stated_ranges(cross):
+    """Two parents that differ in every slot make each child pair's cut points
+    readable: every cut lies in its stated range and, over 300 pairs, both ends
+    of each range occur (single point: [S/4, 3S/4]; two points: [S/4, S/2] and
+    [S/2, 3S/4])."""
+    S = 64
+    prm = oga.GAParams(n_slots=S, d_max=8, total_cap=10_000, min_gap=1, n_elite=0, n_parents=2, crossover=cross,
+                       mutations=0)
+    P = 600
+    pop = np.zeros((P, S), dtype=np.uint8)
+    pop[:, :] = 1
+    pop[0] = 1 + np.arange(S) % 4
+    pop[1] = 5 + np.arange(S) % 4
+    fit = np.zeros(P, dtype=np.float32)
+    fit[:2] = [2.0, 1.0]  # the two parents
+    nxt, _, parents = oga.generation(pop, fit, prm, SEED, 4)
+    assert sorted(parents) == [0, 1]
+    c1s, c2s = [], []
+    for m in range(P // 2):
+        c0 = nxt[2 * m]
+        a_first = c0[0] == pop[0][0]
+        other = pop[1] if a_first else pop[0]
+        inside = np.flatnonzero(c0 == other)
+        if cross == oga.X_SINGLE:
+            assert inside.size and inside[-1] == S - 1 and np.array_equal(inside, np.arange(inside[0], S))
+            c1s.append(int(inside[0]))
+        else:
+            if inside.size == 0:  # c1 == c2: no middle segment
+                continue
+            assert np.array_equal(inside, np.arange(inside[0], inside[-1] + 1))
+            c1s.append(int(inside[0]))
+            c2s.append(int(inside[-1]) + 1)
+    if cross == oga.X_SINGLE:
+        assert min(c1s) == S // 4 and max(c1s) == 3 * S // 4
+    else:
+        assert min(c1s) == S // 4 and max(c1s) == S // 2
+        assert min(c2s) == S // 2 and max(c2s) == 3 * S // 4
