@@ -56,10 +56,11 @@ def workload():
     if WORKLOAD == "single":
         prot = [workloads.daily_fractions(10, 2.0, 24.0)]
         return prot, 288.0, np.array([40], dtype=np.int32), np.array([5], dtype=np.int32)
+    rank = int(os.environ.get("RANK", "0"))  # under torchrun every rank evaluates its own protocols
     if WORKLOAD == "ragged":
-        Ls, Rs, prot = workloads.ragged_batch(N_PROT, seed=3)
+        Ls, Rs, prot = workloads.ragged_batch(N_PROT, seed=3 + 1000 * rank)
     else:
-        prot = workloads.ga_batch(N_PROT, seed=2)
+        prot = workloads.ga_batch(N_PROT, seed=2 + 1000 * rank)
         Ls, Rs = np.full(N_PROT, L, dtype=np.int32), np.full(N_PROT, R, dtype=np.int32)
     t_end_h = [sum(w) + 120.0 for _, w in prot]
     return prot, float(np.mean(t_end_h)), Ls, Rs
