@@ -53,6 +53,11 @@ def test_workspace_size_validation(lib):
     assert lib.sim_workspace_size(ctypes.byref(cfg), 0, Lp, ctypes.byref(size)) == -1
     unstable = make_config(P0.replace(lam=(0.2, 0.05, 0.1)))
     assert lib.sim_workspace_size(ctypes.byref(unstable), 2, Lp, ctypes.byref(size)) == -1
+    for bad_params in (P0.replace(repair_half_h=-1.0), P0.replace(repair_half_h=float("nan")),
+                       P0.replace(n_sub=0), P0.replace(n_sub=257)):
+        cfg_bad = make_config(bad_params)
+        assert lib.sim_workspace_size(ctypes.byref(cfg_bad), 2, Lp, ctypes.byref(size)) == -1
+    assert lib.sim_workspace_size(ctypes.byref(make_config(P0.replace(n_sub=256))), 2, Lp, ctypes.byref(size)) == 0
     half = make_config(P0, precision="bf16", hours=10)
     s2 = ctypes.c_size_t()
     assert lib.sim_workspace_size(ctypes.byref(half), 2, Lp, ctypes.byref(s2)) == 0
