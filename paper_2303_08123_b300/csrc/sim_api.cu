@@ -288,10 +288,10 @@ void launch_fused_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, c
 }
 
 // the one-column-per-thread kernel of storage type T: k_fused1 for FP32, k_fused1h for 2-byte types
-template <typename T, int TX, int TY, int K, bool EPI>
+template <typename T, int TX, int TY, int K, bool EPI, bool FULL>
 constexpr auto fused1_kernel() {
-    if constexpr (std::is_same<T, float>::value) return k_fused1<TX, TY, K, EPI>;
-    else return k_fused1h<T, TX, TY, K, EPI>;
+    if constexpr (std::is_same<T, float>::value) return k_fused1<TX, TY, K, EPI, FULL>;
+    else return k_fused1h<T, TX, TY, K, EPI, FULL>;
 }
 template <typename T, int TX, int TY, int K>
 constexpr size_t fused1_bytes() {
@@ -299,11 +299,11 @@ constexpr size_t fused1_bytes() {
     else return fused1h_smem_bytes<T, TX, TY, K>();
 }
 
-template <typename T, int TX, int TY, int K, bool EPI>
-void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin,
+template <typename T, int TX, int TY, int K, bool EPI, bool FULL>
+void launch_fused1_f(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin,
                      uint32_t* cout, int pass) {
     using Sh = FusedShape1<TX, TY, K>;
-    constexpr auto kern = fused1_kernel<T, TX, TY, K, EPI>();
+    constexpr auto kern = fused1_kernel<T, TX, TY, K, EPI, FULL>();
     static unsigned grid = 0;
     if (!grid) grid = persistent_grid(kern, Sh::THREADS, fused1_bytes<T, TX, TY, K>(), ~0ull);
     const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
@@ -314,6 +314,16 @@ void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, 
         c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
         c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr),
         (int)c->tiles.size(), pass, c->P);
+}
+
+// diffusion and reaction on (the model as run): the instance with both switches fixed at compile time
+template <typename T, int TX, int TY, int K, bool EPI>
+void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin,
+                     uint32_t* cout, int pass) {
+    if ((c->P.flags & (kFDiffusion | kFReaction)) == (kFDiffusion | kFReaction))
+        launch_fused1_f<T, TX, TY, K, EPI, true>(c, s, k_off, first, buf, cin, cout, pass);
+    else
+        launch_fused1_f<T, TX, TY, K, EPI, false>(c, s, k_off, first, buf, cin, cout, pass);
 }
 
 template <typename T, int K, bool EPI>
@@ -342,19 +352,26 @@ cudaError_t fused_attrs_shape() {
     return e;
 }
 
-template <typename T, int TX, int TY>
-cudaError_t fused1_attrs_shape() {
-    cudaError_t e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 1, false>(),
+template <typename T, int TX, int TY, bool FULL>
+cudaError_t fused1_attrs_full() {
+    cudaError_t e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 1, false, FULL>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused1_bytes<T, TX, TY, 1>());
     if (!e)
-        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 1, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused1_bytes<T, TX, TY, 1>());
+        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 1, true, FULL>(),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused1_bytes<T, TX, TY, 1>());
     if (!e)
-        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 2, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused1_bytes<T, TX, TY, 2>());
+        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 2, false, FULL>(),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused1_bytes<T, TX, TY, 2>());
     if (!e)
-        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 2, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused1_bytes<T, TX, TY, 2>());
+        e = cudaFuncSetAttribute(fused1_kernel<T, TX, TY, 2, true, FULL>(),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused1_bytes<T, TX, TY, 2>());
+    return e;
+}
+
+template <typename T, int TX, int TY>
+cudaError_t fused1_attrs_shape() {
+    cudaError_t e = fused1_attrs_full<T, TX, TY, true>();
+    if (!e) e = fused1_attrs_full<T, TX, TY, false>();
     return e;
 }
 

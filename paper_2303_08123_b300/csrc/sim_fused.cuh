@@ -442,7 +442,9 @@ constexpr size_t fused1_smem_bytes() {
 #define SIM_FUSED1_MIN_BLOCKS_LARGE 1  // the same for the 32 x 16 column kernel
 #endif
 
-template <int TX, int TY, int K, bool EPI>
+// FULL: diffusion and reaction both on (the model as run), so their switches
+// are compile-time constants; other switch settings run the FULL = false instance.
+template <int TX, int TY, int K, bool EPI, bool FULL>
 __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                                   (TX * TY <= 256) ? SIM_FUSED1_MIN_BLOCKS_SMALL : SIM_FUSED1_MIN_BLOCKS_LARGE)
     k_fused1(const Tile* __restrict__ tiles, const Proto* __restrict__ protos, const int64_t* __restrict__ clock,
@@ -479,7 +481,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     float* const my_lvh = lv_h + tid;          // + ((l - 1) * 2 + parity) * NC
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
-    const bool diffuse = (P.flags & kFDiffusion) != 0, react = (P.flags & kFReaction) != 0;
+    const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
 
     const int64_t step = *clock + k_off;
     uint32_t* cnt = icount + (step & 1);

@@ -35,7 +35,8 @@ constexpr size_t fused1h_smem_bytes() {
            (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::NC * sizeof(float);
 }
 
-template <typename T, int TX, int TY, int K, bool EPI>
+// FULL as in k_fused1: diffusion and reaction switches fixed on at compile time.
+template <typename T, int TX, int TY, int K, bool EPI, bool FULL>
 __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                                   (TX * TY <= 256) ? SIM_FUSED1_MIN_BLOCKS_SMALL : SIM_FUSED1_MIN_BLOCKS_LARGE)
     k_fused1h(const Tile* __restrict__ tiles, const Proto* __restrict__ protos, const int64_t* __restrict__ clock,
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     float* const my_lvh = lv_h + tid;
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
-    const bool diffuse = (P.flags & kFDiffusion) != 0, react = (P.flags & kFReaction) != 0;
+    const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
     // stochastic-rounding salt of this pass, as in the column-pair kernel
     const uint32_t salt = 3u * (EPI ? (uint32_t)P.n_sub - 1u : (uint32_t)K - 1u) + 100u;
 
