@@ -126,9 +126,10 @@ def evolve_on_device(sim, dga: DeviceGA, generations: int, seed: int, unit_gy: f
     """The paper's main GA loop with every step on the device: load the
     population's dose vectors into the simulator, run every protocol to the
     fixed horizon, score (fitness = n_max - final count), breed the next
-    population.  The host only enqueues work; it reads back the best fitness
-    of each generation once at the end.  Returns (final population, fitness
-    history tensor [generations + 1, P] on the device)."""
+    population.  The host only enqueues work (the simulator synchronises only
+    when its work list changes, which a fixed horizon never causes); nothing is
+    read back until the caller reads the results.  Returns (final population,
+    fitness history tensor [generations + 1, P] on the device)."""
     import torch
 
     pop = dga.random_population(seed) if pop is None else pop
