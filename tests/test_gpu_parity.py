@@ -455,3 +455,32 @@ def test_two_byte_storage_same_on_every_tile_shape(cuda, precision):
         for a, b in zip(out[0], other):
             for x, y in zip(a, b):
                 assert np.array_equal(x, y)
+
+
+def test_full_size_ragged_batch_in_bench_configuration(cuda, orc):
+    """The ragged bench workload at full size (1,024 protocols, radii 4-20 on
+    32^3-112^3 lattices, autotuned persistent fused path, one hour graph):
+    sampled protocols of every lattice size equal the oracle after 600 steps
+    (cells and hourly counts bit for bit, fields within 1e-4 of the medium)."""
+    from paper_2303_08123_b300 import Simulator, csr
+    from synth import workloads
+    L, R, prot = workloads.ragged_batch(1024, seed=3)
+    first = {}
+    for p, l in enumerate(L):
+        first.setdefault(int(l), p)
+    sample = [first[l] for l in sorted(first) if l <= 64]  # the oracle finishes these in seconds
+    for p in sample:  # a fraction inside the hour for the sampled slots
+        prot[p] = ([min(prot[p][0][0], 5.0)] + prot[p][0][1:], [0.5] + prot[p][1][1:])
+    sim = Simulator(L, R, seed=SEED, hours=2, dose_cap_gy=30.0)
+    sim.load_protocols(*csr(prot))
+    sim.autotune(2)
+    sim.run(600)
+    for p in sample:
+        d, w = prot[p]
+        ref = orc.run(P0, int(L[p]), int(R[p]), SEED, p, d, w, t_end_steps=600, hours=1)
+        O, G, H, cell = sim.get_state(p)
+        assert np.array_equal(cell, ref["state"].cell), (p, int(L[p]), ref["stats"])
+        for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
+            assert np.max(np.abs(g - o)) / m < 1e-4
+        assert np.array_equal(sim.counts()[p][:2], ref["counts"][:2])
+    assert len(sample) == 3  # lattices 32, 48 and 64
