@@ -1,15 +1,19 @@
 """Throughput benchmark: GA protocols evaluated per second on one B300.
 
-Workload (per GPU): a GA population of 256 protocols on identical 64^3
-lattices, each starting from the same seeded spheroid of radius 8 (2,109
-cells); 10 fractions per protocol with doses from {0.5, ..., 2.5} Gy and waits
-from {6, ..., 60} h, total dose capped at 20 Gy; FP32 fields; horizon = last
-fraction + 120 h.  A bench step is one simulated hour (600 CA steps) of the
-whole batch, all hot-path kernels included (irradiation, reaction-diffusion,
-cell update, division, hourly counts).  protocols/s = protocol-steps per second
-divided by the batch's mean horizon in steps.
+Default workload (per GPU): the ragged hypofractionated batch, 1,024 protocols
+whose spheroid radius is uniform in 4-20 sites on lattices of side
+16 ceil(5R/16) (32^3 to 112^3); 5-15 fractions per protocol with doses from
+{1, ..., 5} Gy and waits from {6, ..., 60} h, total dose capped at 30 Gy; FP32
+fields; horizon = last fraction + 120 h.  A bench step is one simulated hour
+(600 CA steps) of the whole batch, all hot-path kernels included (irradiation,
+reaction-diffusion, cell update, division, hourly counts).  The batch is first
+advanced, untimed, to --start-hour (the last W of those hours are the warm-up),
+so the timed window does not sit on the cheap hours right after seeding.
+protocols/s = protocol-steps per second of the window divided by the batch's
+mean horizon in steps (an extrapolation, labelled so in the line).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ragged|ga_batch|single] [--start-hour H]
 
 N > 1 runs under torchrun, one batch per rank (weak scaling, no collective on
 the data path).  `--impl reference` times the FP64 CPU oracle on this host's
@@ -42,8 +46,10 @@ UNIT = "protocols/s"
 STEPS_PER_HOUR = 600
 
 
-WORKLOAD = "ga_batch"
+WORKLOAD = "ragged"
 PARAMS, PARAMS_NOTE = P0, ""
+START_HOUR = 24
+CPU_SAMPLE_STEPS = {"ragged": 100, "single": 6000}  # oracle steps per protocol of one CPU sample
 
 
 def t_end_steps():
@@ -86,9 +92,9 @@ def workload_config(mean_t_end_h, precision="fp32"):
                         "5-15 fractions of {1..5} Gy, waits {6..60} h, cap 30 Gy, "
                         f"{precision} fields, n_sub={PARAMS.n_sub}" + PARAMS_NOTE,
             "step": "one simulated hour (600 CA steps) of the whole batch",
-            "protocols_per_s": "protocol-steps/s of the timed hours (right after the seeded start) divided by "
-                               "the mean horizon (last fraction + 120 h): extrapolated; later hours cost more as "
-                               "the tumours grow, --full-run times the whole batch",
+            "timed_window": f"hours {START_HOUR}..{START_HOUR}+K after the seeded start (advanced untimed first)",
+            "protocols_per_s": "protocol-steps/s of the timed window divided by the mean horizon (last fraction "
+                               "+ 120 h): extrapolated from that window",
             "mean_horizon_h": round(mean_t_end_h, 2),
             "l2": "working set > 126 MB L2: no flush needed",
             "parallelism": "independent protocol batch per GPU, persistent tile scheduling",
@@ -98,9 +104,9 @@ def workload_config(mean_t_end_h, precision="fp32"):
                     "10 fractions/protocol, doses {0.5..2.5} Gy, waits {6..60} h, cap 20 Gy, "
                     f"{precision} fields, n_sub={PARAMS.n_sub}" + PARAMS_NOTE,
         "step": "one simulated hour (600 CA steps) of the whole batch",
-        "protocols_per_s": "protocol-steps/s of the timed hours (right after the seeded start) divided by the "
-                           "mean horizon (last fraction + 120 h): extrapolated; later hours cost more as the "
-                           "tumours grow, --full-run times the whole batch",
+        "timed_window": f"hours {START_HOUR}..{START_HOUR}+K after the seeded start (advanced untimed first)",
+        "protocols_per_s": "protocol-steps/s of the timed window divided by the mean horizon (last fraction + "
+                           "120 h): extrapolated from that window; --full-run times the whole batch",
         "mean_horizon_h": round(mean_t_end_h, 2),
         "l2": "working set > 126 MB L2 (fields alone 805 MB at 256 protocols): no flush needed",
         "parallelism": "independent protocol batch per GPU",
@@ -204,7 +210,7 @@ def cpu_baseline(mean_t_end_h, max_steps=None):
     cores = os.cpu_count() or 1
     prot, _, Ls, Rs = workload()
     n = min(cores, N_PROT)
-    steps = max_steps or {"ragged": 300, "single": 6000}.get(WORKLOAD, 1200)
+    steps = max_steps or CPU_SAMPLE_STEPS.get(WORKLOAD, 1200)
     off, d, w = _csr(prot[:n])
     t0 = time.perf_counter()
     res = oracle.run_batch(PARAMS, Ls[:n], Rs[:n], SEED, off, d, w, max_steps=steps, n_threads=n)
@@ -217,6 +223,41 @@ def cpu_baseline(mean_t_end_h, max_steps=None):
             "site_steps_per_s": site_steps / dt}
 
 
+def precision_error(precision, n, steps):
+    """Oracle leg of a 2-byte-storage run, outside every timed region: n seeded
+    protocols of the GA-batch generator on 64^3 (R = 8, first wait 30 min so a
+    fraction falls inside the window) run `steps` steps on the GPU with this
+    storage and on the FP64 oracle (host threads).  Maximum field error
+    relative to the medium value, and live-count errors."""
+    import oracle
+    from paper_2303_08123_b300 import Simulator, csr
+    Lq, Rq, seed = 64, 8, 0x5EED_0004
+    prot = [(dd, [0.5] + ww[1:]) for dd, ww in workloads.ga_batch(n, seed=4)]
+    off, d, w = csr(prot)
+    ref = oracle.run_batch(PARAMS, [Lq] * n, [Rq] * n, seed, off, d, w, t_end_steps=steps)
+    sample = list(range(0, n, max(1, n // 4)))
+    ref_state = {p: oracle.run(PARAMS, Lq, Rq, seed, p, prot[p][0], prot[p][1], t_end_steps=steps)["state"]
+                 for p in sample}
+    med = np.array([PARAMS.medium_O, PARAMS.medium_G, 10 ** (3 - PARAMS.medium_pH)])
+    sim = Simulator([Lq] * n, [Rq] * n, seed=seed, precision=precision, t_end_steps=steps, dose_cap_gy=20.0,
+                    params=PARAMS)
+    sim.load_protocols(off, d, w)
+    sim.run(0)
+    cnt, _ = sim.fitness()
+    ferr = np.zeros(3)
+    for p in sample:
+        st = ref_state[p]
+        got = sim.get_state(p)[:3]
+        ferr = np.maximum(ferr, [float(np.max(np.abs(a.astype(np.float64) - b))) / m
+                                 for a, b, m in zip(got, (st.O, st.G, st.H), med)])
+    sim.close()
+    cerr = np.abs(cnt.astype(np.float64) - ref["n_final"]) / np.maximum(1, ref["n_final"])
+    return {"sample": f"{n} GA-batch protocols on 64^3 (R=8), {steps} steps from the seeded start, oracle FP64; "
+                      f"fields compared on {len(sample)} of them",
+            "field_err_max_rel_medium": {k: float(v) for k, v in zip("OGH", ferr)},
+            "count_err_max_rel": float(cerr.max()), "count_exact_fraction": float(np.mean(cnt == ref["n_final"]))}
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -224,11 +265,12 @@ def run_reference(args):
         return 0
     prot, mean_h, _, _ = workload()
     vals = []
+    # each step: the same bounded oracle sample as the cpu_baseline of our arm's line
     for _ in range(args.warmup):
         cpu_baseline(mean_h, max_steps=20)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(mean_h, max_steps=40))
+        vals.append(cpu_baseline(mean_h))
     ms_per_step = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
     v = statistics.mean(x["value"] for x in vals)
     cb = dict(vals[-1])
@@ -259,7 +301,8 @@ def run_ours(args):
     prot, mean_h, Ls, Rs = workload()
     off, d, w = csr(prot)
     K, W = args.steps, args.warmup
-    hours = W + K + 2
+    start_h = max(START_HOUR, W)  # the timed window opens at this hour; the last W hours before it are warm-up
+    hours = start_h + K + 2
 
     def barrier():
         if world > 1:
@@ -277,6 +320,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     if args.full_run:
         return full_run(args, sim, prot, mean_h, Ls, shape, shape_ms, world, rank, dev, barrier)
+    sim.run(STEPS_PER_HOUR * (start_h - W))  # untimed advance to the warm-up hours
     for _ in range(W):
         sim.run(STEPS_PER_HOUR)
     barrier()
@@ -305,7 +349,8 @@ def run_ours(args):
     interior = float(np.sum((Ls.astype(np.float64) - 2) ** 3))
     es = 4 if args.precision == "fp32" else 2
     if args.path == "fused":
-        kn = ("k_fused1" if args.precision == "fp32" else "k_fused1h") if shape in (3, 4) else "k_fused"
+        kn = ("k_tma" if shape in (5, 6) else
+              ("k_fused1" if args.precision == "fp32" else "k_fused1h") if shape in (3, 4) else "k_fused")
         classes = {f"{kn} (first pass: irradiation + 2 substeps)": (kms[0], kl[0], interior * (6 * es + 4)),
                    f"{kn} (last pass: 2 substeps + cell update)": (kms[1], kl[1], interior * (6 * es + 8))}
         traffic_key = {f"{kn} (first pass: irradiation + 2 substeps)": f"{kn}_first_shape{shape}",
@@ -331,18 +376,20 @@ def run_ours(args):
                  "achieved_GBps": site_steps_per_s / world * step_bytes / 1e9,
                  "frac": site_steps_per_s / world * step_bytes / 1e9 / hbm}
 
-    # end to end through the public API with host buffers: protocol table H2D
-    # (and spheroid reseed) inside the timed region, fitness read back every step
+    # end to end through the public API with host buffers: the protocol table
+    # H2D (and spheroid reseed) inside the timed region, then E simulated hours
+    # from the seeded start, the fitness read back after every hour
+    E = min(K, 5)
     barrier()
     t0 = time.perf_counter()
     sim.load_protocols(off, d, w)
-    for _ in range(K):
+    for _ in range(E):
         sim.run(STEPS_PER_HOUR)
         cnt, fit = sim.fitness()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_val = world * N_PROT * STEPS_PER_HOUR * K / e2e_s / (mean_h * STEPS_PER_HOUR)
-    h2d = (off.nbytes + d.nbytes + w.nbytes) / K
+    e2e_val = world * N_PROT * STEPS_PER_HOUR * E / e2e_s / (mean_h * STEPS_PER_HOUR)
+    h2d = (off.nbytes + d.nbytes + w.nbytes) / E
     d2h = cnt.nbytes + fit.nbytes
 
     # plain form: one protocol at a time, per-step launches, no graph
@@ -371,9 +418,13 @@ def run_ours(args):
                 "roofline": roof, "step_roofline": roof_step,
                 "plain": {"value": plain_val, "unit": UNIT,
                           "how": "one protocol per launch sequence, per-step launches, no graph"},
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": E, "window": f"hours 0..{E} after sim_load_protocols (the load, its H2D copy "
+                                              "and the re-seeding inside the timed region)"},
                 "gpu_launches": launches_per_step * K,
                 "clocks": clk.summary()}
+        if args.precision != "fp32":
+            line["error_vs_oracle"] = precision_error(args.precision, args.error_sample, args.error_steps)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(mean_h)
         print(json.dumps(line))
@@ -436,21 +487,29 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "substep"])
     ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-4 (0: autotune)")
-    ap.add_argument("--workload", default="ga_batch", choices=["ga_batch", "ragged", "single"],
-                    help="ga_batch: 256 x 64^3 (default); ragged: 1,024 protocols on 32^3-112^3; "
+    ap.add_argument("--workload", default="ragged", choices=["ga_batch", "ragged", "single"],
+                    help="ragged: 1,024 protocols on 32^3-112^3 (default); ga_batch: 256 x 64^3; "
                          "single: one protocol on 40^3 for 288 h")
-    ap.add_argument("--protocols", type=int, default=256, help="batch size per GPU (smaller: profiling cases)")
+    ap.add_argument("--start-hour", type=int, default=None,
+                    help="simulated hour at which the timed window opens (default 24; 0 for --workload single)")
+    ap.add_argument("--error-sample", type=int, default=8,
+                    help="2-byte storage: protocols checked against the oracle for error_vs_oracle")
+    ap.add_argument("--error-steps", type=int, default=1200,
+                    help="2-byte storage: steps of the error_vs_oracle check")
+    ap.add_argument("--protocols", type=int, default=None,
+                    help="batch size per GPU (default 1,024 ragged, 256 ga_batch; smaller: profiling cases)")
     ap.add_argument("--params", default="p0", choices=["p0", "phys"],
                     help="p0: coarse-grained diffusion (4 substeps per step); phys: physical-rate variant "
                          "(128 substeps per step)")
     ap.add_argument("--full-run", action="store_true",
                     help="time the whole batch to every horizon (about ten minutes for the default workload)")
     args = ap.parse_args()
-    global N_PROT, WORKLOAD, PARAMS, PARAMS_NOTE
+    global N_PROT, WORKLOAD, PARAMS, PARAMS_NOTE, START_HOUR
     WORKLOAD = args.workload
+    START_HOUR = args.start_hour if args.start_hour is not None else (0 if args.workload == "single" else 24)
     if args.params == "phys":
         PARAMS, PARAMS_NOTE = P_PHYS, " (physical-rate diffusion variant, uptake per substep scaled by 4/128)"
-    N_PROT = args.protocols if not (args.workload == "ragged" and args.protocols == 256) else 1024
+    N_PROT = args.protocols if args.protocols else (1024 if args.workload == "ragged" else 256)
     if args.workload == "single":
         N_PROT = 1
     if args.impl == "reference":

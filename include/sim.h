@@ -87,7 +87,9 @@ typedef struct {
     int32_t path;           /* SIM_PATH_FUSED (default) or SIM_PATH_SUBSTEP */
     int32_t tile_shape;     /* fused tile: 0 auto; 1 = 32 x 16, 2 = 16 x 16 with two columns per
                                thread (packed FP32); 3 = 32 x 16, 4 = 16 x 16 with one column per
-                               thread.  For a given storage precision every shape gives the same
+                               thread; 5 = 32 x 16, 6 = 16 x 16 with one column per thread and the
+                               planes staged by TMA (FP32 storage, every lattice side a multiple of
+                               4).  For a given storage precision every shape gives the same
                                results bit for bit */
     int32_t z_chunk;        /* fused z range per CTA: 0 auto, else planes per CTA */
 } sim_config;
@@ -241,24 +243,28 @@ sim_status sim_profile_steps(sim_ctx* ctx, int n_steps, double* ms, int64_t* lau
  *  - Sizes: 8 <= L <= 64.  A larger lattice is rejected with SIM_ENOSPC
  *    before any work is enqueued; cfg->precision must be SIM_FP32.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins.
+ *    (cudaGetSymbolAddress) with that device current, and looks it up again
+ *    when the device's context has changed (after a cudaDeviceReset).
+ *  - The small launch tables are copied from host memory that lives only
+ *    during the call, so a call on a stream that is being captured is
+ *    refused with SIM_EINVAL before any work is enqueued.
  *  - All calls share the one array and each call overwrites it (it keeps the
  *    last call's contents): calls that overlap on the GPU, e.g. on two
  *    streams, race and corrupt each other's results.  Serialise them.
  *  - No device memory is allocated or freed; the call is asynchronous.
- * Errors: SIM_EINVAL (NULL pointer, bad config, negative dose or step),
- * SIM_ENOSPC (L > 64), SIM_ECUDA.
+ * Errors: SIM_EINVAL (NULL pointer, bad config, negative dose or step, a
+ * stream under capture), SIM_ENOSPC (L > 64), SIM_ECUDA (a failed copy or
+ * launch of this call; errors pending from earlier work are left untouched).
  */
 sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, double dose_gy, float* O, float* G,
                                float* H, uint32_t* cell, void* cuda_stream);
 
 /*
  * Autotuner of the fused path: time n_steps plain steps of this context's own
- * batch with every applicable tile shape (sim_config.tile_shape 1..4), keep the
+ * batch with every applicable tile shape (sim_config.tile_shape 1..6), keep the
  * fastest, then re-seed every spheroid and set the clock to 0 (call it right
  * after sim_load_protocols).  *best (may be NULL) receives the chosen shape
- * (0 on the substep path); ms (4 entries, may be NULL) the device milliseconds
+ * (0 on the substep path); ms (6 entries, may be NULL) the device milliseconds
  * per step of each shape, -1 where a shape does not apply.  Synchronises.
  */
 sim_status sim_autotune(sim_ctx* ctx, int n_steps, int* best, double* ms);

@@ -110,6 +110,8 @@ def lib():
         L.or_run.argtypes = [P(_Params), ctypes.c_int, ctypes.c_int, u32p, ctypes.c_uint32, ctypes.c_uint32,
                              ctypes.c_int, f64p, f64p, ctypes.c_int64, ctypes.c_int, i32p, ctypes.c_int,
                              f64p, f64p, f64p, u32p, f64p, P(_Stats)]
+        L.or_run_near.restype = ctypes.c_int64
+        L.or_run_near.argtypes = L.or_run.argtypes + [u8p]
         L.or_run_batch.restype = ctypes.c_int
         L.or_run_batch.argtypes = [P(_Params), ctypes.c_int, i32p, i32p, u32p, u32p, ctypes.c_uint32, i32p,
                                    f64p, f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, i64p, i64p, i32p,
@@ -186,8 +188,9 @@ def fraction_steps(wait_h) -> np.ndarray:
 
 
 def run(p: Params, L: int, R: int, seed: int, protocol: int, doses, waits, t_end_steps: int = 0,
-        regrowth_h: int = 120, hours: int = 0, init_word: int = 0xFFFFFFFF):
-    """Whole run from the seeded spheroid.  Returns dict(counts, state, steps, cum_dose, stats)."""
+        regrowth_h: int = 120, hours: int = 0, init_word: int = 0xFFFFFFFF, near: bool = False):
+    """Whole run from the seeded spheroid.  Returns dict(counts, state, steps, cum_dose, stats), and with
+    near=True also near_any: per site the OR of the near-threshold flags of every step of the run."""
     pk = _pack(p)
     d = np.ascontiguousarray(doses, dtype=np.float64)
     w = np.ascontiguousarray(waits, dtype=np.float64)
@@ -195,12 +198,17 @@ def run(p: Params, L: int, R: int, seed: int, protocol: int, doses, waits, t_end
     st = State(L)
     cum = ctypes.c_double(0.0)
     tot = _Stats()
-    T = lib().or_run(ctypes.byref(pk), L, R, _ptr(_key(seed), ctypes.c_uint32), protocol, init_word, len(d),
-                     _ptr(d, ctypes.c_double), _ptr(w, ctypes.c_double), int(t_end_steps), int(regrowth_h),
-                     _ptr(counts, ctypes.c_int32), hours, _ptr(st.O, ctypes.c_double), _ptr(st.G, ctypes.c_double),
-                     _ptr(st.H, ctypes.c_double), _ptr(st.cell, ctypes.c_uint32), ctypes.byref(cum),
-                     ctypes.byref(tot))
-    return dict(counts=counts, state=st, steps=int(T), cum_dose=cum.value, stats=tot.as_dict())
+    args = (ctypes.byref(pk), L, R, _ptr(_key(seed), ctypes.c_uint32), protocol, init_word, len(d),
+            _ptr(d, ctypes.c_double), _ptr(w, ctypes.c_double), int(t_end_steps), int(regrowth_h),
+            _ptr(counts, ctypes.c_int32), hours, _ptr(st.O, ctypes.c_double), _ptr(st.G, ctypes.c_double),
+            _ptr(st.H, ctypes.c_double), _ptr(st.cell, ctypes.c_uint32), ctypes.byref(cum), ctypes.byref(tot))
+    out = {}
+    if near:
+        out["near_any"] = np.zeros(L ** 3, dtype=np.uint8)
+        T = lib().or_run_near(*args, _ptr(out["near_any"], ctypes.c_uint8))
+    else:
+        T = lib().or_run(*args)
+    return dict(counts=counts, state=st, steps=int(T), cum_dose=cum.value, stats=tot.as_dict(), **out)
 
 
 def run_batch(p: Params, L, R, seed: int, offsets, doses, waits, p_words=None, t_end_steps: int = 0,

@@ -399,8 +399,11 @@ static void add_stats(or_stats* a, const or_stats* b) {
 static int64_t run_impl(const or_params* P, int L, int R, const uint32_t key[2], uint32_t protocol,
                         uint32_t init_word, int n_frac, const double* dose_gy, const double* wait_h,
                         int64_t t_end_steps, int regrowth_h, int64_t max_steps, int32_t* counts, int hours,
-                        double* O, double* G, double* H, uint32_t* cell, double* cum_dose, or_stats* total) {
+                        double* O, double* G, double* H, uint32_t* cell, double* cum_dose, or_stats* total,
+                        uint8_t* near_any) {
     const int64_t N = (int64_t)L * L * L;
+    uint8_t* near = near_any ? (uint8_t*)malloc((size_t)N) : NULL;
+    if (near_any) memset(near_any, 0, (size_t)N);
     int64_t* fstep = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_frac > 0 ? n_frac : 1));
     for (int j = 0; j < n_frac; ++j) fstep[j] = or_fraction_step(wait_h, j);
     int64_t T = t_end_steps > 0 ? t_end_steps : (n_frac > 0 ? fstep[n_frac - 1] : 0) + 600LL * regrowth_h;
@@ -422,13 +425,15 @@ static int64_t run_impl(const or_params* P, int L, int R, const uint32_t key[2],
         }
         cum += dose;
         or_stats st;
-        or_step(P, L, OR_BC_DIRICHLET, key, protocol, (uint32_t)s, dose, unrepaired, O, G, H, cell, NULL, &st);
+        or_step(P, L, OR_BC_DIRICHLET, key, protocol, (uint32_t)s, dose, unrepaired, O, G, H, cell, near, &st);
+        if (near_any)
+            for (int64_t i = 0; i < N; ++i) near_any[i] |= near[i];
         add_stats(&tot, &st);
         live = st.n_live;
     }
     if (counts && T % 600 == 0 && T / 600 <= hours) counts[T / 600] = (int32_t)live;
     tot.n_live = live;
-    (void)N;
+    free(near);
     free(fstep);
     if (cum_dose) *cum_dose = cum;
     if (total) *total = tot;
@@ -440,7 +445,15 @@ int64_t or_run(const or_params* P, int L, int R, const uint32_t key[2], uint32_t
                int32_t* counts, int hours, double* O, double* G, double* H, uint32_t* cell, double* cum_dose,
                or_stats* total) {
     return run_impl(P, L, R, key, protocol, init_word, n_frac, dose_gy, wait_h, t_end_steps, regrowth_h, 0,
-                    counts, hours, O, G, H, cell, cum_dose, total);
+                    counts, hours, O, G, H, cell, cum_dose, total, NULL);
+}
+
+int64_t or_run_near(const or_params* P, int L, int R, const uint32_t key[2], uint32_t protocol,
+                    uint32_t init_word, int n_frac, const double* dose_gy, const double* wait_h,
+                    int64_t t_end_steps, int regrowth_h, int32_t* counts, int hours, double* O, double* G,
+                    double* H, uint32_t* cell, double* cum_dose, or_stats* total, uint8_t* near_any) {
+    return run_impl(P, L, R, key, protocol, init_word, n_frac, dose_gy, wait_h, t_end_steps, regrowth_h, 0,
+                    counts, hours, O, G, H, cell, cum_dose, total, near_any);
 }
 
 /* ------------------------------------------------------------------ */
@@ -475,7 +488,7 @@ static void* batch_worker(void* arg) {
         const uint32_t iw = J->init_word == 0xFFFFFFFEu ? J->p_word[p] : J->init_word;
         int64_t T = run_impl(J->P, L, J->R[p], J->key, J->p_word[p], iw, nf, J->dose + J->off[p],
                              J->wait + J->off[p], J->t_end, J->regrowth_h, J->max_steps, cnt, J->hours, f,
-                             f + N, f + 2 * N, cell, NULL, &tot);
+                             f + N, f + 2 * N, cell, NULL, &tot, NULL);
         J->n_final[p] = tot.n_live;
         J->steps[p] = T;
         free(f);

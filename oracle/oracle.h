@@ -82,6 +82,15 @@ int64_t or_run(const or_params* P, int L, int R, const uint32_t key[2], uint32_t
                double* O, double* G, double* H, uint32_t* cell, double* cum_dose,
                or_stats* total);
 
+/* or_run, and near_any (L^3 entries) receives per site the OR of the
+ * OR_NEAR_* bits of every step of the run: the sites where some decision of
+ * the run fell inside the near-threshold band. */
+int64_t or_run_near(const or_params* P, int L, int R, const uint32_t key[2], uint32_t protocol,
+                    uint32_t init_word, int n_frac, const double* dose_gy, const double* wait_h,
+                    int64_t t_end_steps, int regrowth_h, int32_t* counts, int hours,
+                    double* O, double* G, double* H, uint32_t* cell, double* cum_dose,
+                    or_stats* total, uint8_t* near_any);
+
 /* Many protocols on n_threads host threads (one protocol per thread at a time).
  * Per protocol p: lattice L[p], radius R[p], fractions off[p]..off[p+1]-1,
  * protocol word p_word[p]; init_word 0xFFFFFFFE seeds each protocol's spheroid

@@ -19,6 +19,7 @@
 #include "sim_kernels.cuh"
 #include "sim_fused.cuh"
 #include "sim_fused1h.cuh"
+#include "sim_tma.cuh"
 
 using namespace simdev;
 
@@ -35,10 +36,20 @@ size_t elem_size(int precision) { return precision == SIM_FP32 ? 4 : 2; }
 // Byte offsets of every region of the workspace.
 struct Layout {
     size_t proto, blocks, tiles, fstep, fdose, field[2][3], cell[2], claim, intents, target, icount, counts, cum,
-        clock, status, final_count, first_block, part64, part32, tot64, tot32, tile_ctr, total;
+        clock, status, final_count, first_block, part64, part32, tot64, tot32, tile_ctr, tmaps, total;
 };
 
-Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks, int64_t ntiles) {
+constexpr int kTmaShapes = 2;  // tile shapes 5 (32 x 16) and 6 (16 x 16) stage their planes by TMA
+
+// Number of distinct lattice sides (one set of tensor maps each).
+int side_classes(int n, const int32_t* L) {
+    std::vector<int32_t> u(L, L + n);
+    std::sort(u.begin(), u.end());
+    return (int)(std::unique(u.begin(), u.end()) - u.begin());
+}
+
+Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nblocks, int64_t ntiles,
+                   int n_sides) {
     Layout l{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -72,6 +83,7 @@ Layout make_layout(const sim_config& cfg, int n, int64_t total_sites, int64_t nb
     l.tot64 = take(sizeof(double) * 3 * n);
     l.tot32 = take(sizeof(float) * 3 * n);
     l.tile_ctr = take(sizeof(uint32_t) * 2 * kMaxPasses);
+    l.tmaps = take(sizeof(CUtensorMap) * kTmaShapes * (size_t)n_sides * kTmaArrays);
     l.total = off;
     return l;
 }
@@ -93,15 +105,31 @@ bool valid_config(const sim_config* cfg, std::string* why) {
         return *why = "repair_half_h must be finite and >= 0", false;
     if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
     if (cfg->path < SIM_PATH_FUSED || cfg->path > SIM_PATH_SUBSTEP) return *why = "unknown kernel path", false;
-    if (cfg->tile_shape < 0 || cfg->tile_shape > 4) return *why = "tile_shape must be in 0..4", false;
+    if (cfg->tile_shape < 0 || cfg->tile_shape > 6) return *why = "tile_shape must be in 0..6", false;
     if (cfg->z_chunk < 0) return *why = "z_chunk must be >= 0", false;
     return true;
 }
 
 // Tile shapes of the fused kernels: (x extent, y extent); shapes 1-2 run two
-// columns per thread (packed f32x2), shapes 3-4 one column per thread.
-constexpr int kNumShapes = 4;
-constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0}, {32, 16}, {16, 16}, {32, 16}, {16, 16}};
+// columns per thread (packed f32x2), shapes 3-4 one column per thread, shapes
+// 5-6 one column per thread with the planes staged by TMA (FP32 storage).
+constexpr int kNumShapes = 6;
+constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0}, {32, 16}, {16, 16}, {32, 16}, {16, 16}, {32, 16}, {16, 16}};
+bool tma_shape(int sh) { return sh == 5 || sh == 6; }
+
+// First site of each protocol: the running total rounded up to a multiple of
+// L^2, so that a protocol's planes are whole z-slices of the L x L x Z volume a
+// tensor map of its side describes.  Returns the padded total.
+int64_t place_protocols(int n, const int32_t* L, int64_t* site0) {
+    int64_t at = 0;
+    for (int p = 0; p < n; ++p) {
+        const int64_t LL = (int64_t)L[p] * L[p];
+        at = (at + LL - 1) / LL * LL;
+        if (site0) site0[p] = at;
+        at += LL * L[p];
+    }
+    return at;
+}
 constexpr int kTargetCtas = 2 * 148;  // at least two CTAs per SM when the batch allows it
 
 // Default tile shape (the autotuner may pick any): one column per thread, the
@@ -180,6 +208,8 @@ struct sim_ctx {
     int64_t counted_hour = -1;  // last hour whose counts were recorded
     bool loaded = false;
     cudaGraphExec_t hour_graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by (field, cell) start buffers
+    bool tma_ok = false;  // tensor maps encoded: shapes 5 and 6 may run
+    int n_sides = 0;      // distinct lattice sides (tensor-map classes)
     std::string err;
 
     template <typename T>
@@ -326,9 +356,40 @@ void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, 
         launch_fused1_f<T, TX, TY, K, EPI, false>(c, s, k_off, first, buf, cin, cout, pass);
 }
 
+template <int TX, int TY, int K, bool EPI, bool FULL>
+void launch_tma_f(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, int cbuf, uint32_t* cout, int pass) {
+    using Sh = TmaShape<TX, TY, K>;
+    constexpr auto kern = k_tma<TX, TY, K, EPI, FULL>;
+    static unsigned grid = 0;
+    if (!grid) grid = persistent_grid(kern, Sh::THREADS, tma_smem_bytes<TX, TY, K>(), ~0ull);
+    const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
+    const CUtensorMap* maps =
+        c->at<CUtensorMap>(c->lay.tmaps) + (size_t)(c->shape - 5) * c->n_sides * kTmaArrays;
+    kern<<<g, Sh::THREADS, tma_smem_bytes<TX, TY, K>(), s>>>(
+        c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first, maps,
+        3 * buf, (float*)c->field(buf ^ 1, 0), (float*)c->field(buf ^ 1, 1), (float*)c->field(buf ^ 1, 2), 6 + cbuf,
+        cout, c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
+        c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr),
+        (int)c->tiles.size(), pass, c->P);
+}
+
+template <int TX, int TY, int K, bool EPI>
+void launch_tma_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
+                  int pass) {
+    const int cbuf = cin == c->cells(0) ? 0 : 1;
+    if ((c->P.flags & (kFDiffusion | kFReaction)) == (kFDiffusion | kFReaction))
+        launch_tma_f<TX, TY, K, EPI, true>(c, s, k_off, first, buf, cbuf, cout, pass);
+    else
+        launch_tma_f<TX, TY, K, EPI, false>(c, s, k_off, first, buf, cbuf, cout, pass);
+}
+
 template <typename T, int K, bool EPI>
 void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
                     int pass) {
+    if constexpr (std::is_same<T, float>::value) {  // TMA staging: FP32 storage only
+        if (c->shape == 5) return launch_tma_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+        if (c->shape == 6) return launch_tma_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+    }
     if (c->shape == 3) return launch_fused1_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     if (c->shape == 4) return launch_fused1_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     if (c->shape == 2) launch_fused_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
@@ -375,13 +436,81 @@ cudaError_t fused1_attrs_shape() {
     return e;
 }
 
+template <int TX, int TY, int K, bool FULL>
+cudaError_t tma_attrs_k() {
+    cudaError_t e = cudaFuncSetAttribute(k_tma<TX, TY, K, false, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tma_smem_bytes<TX, TY, K>());
+    if (!e)
+        e = cudaFuncSetAttribute(k_tma<TX, TY, K, true, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_smem_bytes<TX, TY, K>());
+    return e;
+}
+
+template <int TX, int TY>
+cudaError_t tma_attrs_shape() {
+    cudaError_t e = tma_attrs_k<TX, TY, 1, true>();
+    if (!e) e = tma_attrs_k<TX, TY, 2, true>();
+    if (!e) e = tma_attrs_k<TX, TY, 1, false>();
+    if (!e) e = tma_attrs_k<TX, TY, 2, false>();
+    return e;
+}
+
 template <typename T>
 cudaError_t fused_attrs() {
     cudaError_t e = fused_attrs_shape<T, 32, 16>();
     if (!e) e = fused_attrs_shape<T, 16, 16>();
     if (!e) e = fused1_attrs_shape<T, 32, 16>();
     if (!e) e = fused1_attrs_shape<T, 16, 16>();
+    if constexpr (std::is_same<T, float>::value) {
+        if (!e) e = tma_attrs_shape<32, 16>();
+        if (!e) e = tma_attrs_shape<16, 16>();
+    }
     return e;
+}
+
+// Tensor maps of the TMA-staged passes: per tile shape (5, 6), lattice-side
+// class and array (O, G, H of both field buffers, both cell-word buffers), an
+// L x L x Z volume over the whole array (Z = planes of L^2 sites it spans) with
+// a (TX + 8) x (TY + 4) x 1 box; sites outside the volume read as zero.  The
+// encoder is the driver's, reached through the runtime so that the library
+// links against the runtime only.  False if any map cannot be encoded (the TMA
+// shapes are then unavailable).
+bool encode_tensor_maps(sim_ctx* c, const std::vector<int32_t>& sides) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    if (!encode) return false;
+    std::vector<CUtensorMap> maps((size_t)kTmaShapes * sides.size() * kTmaArrays);
+    for (int sh = 0; sh < kTmaShapes; ++sh) {
+        const int TX = kTileShapes[5 + sh][0], TY = kTileShapes[5 + sh][1];
+        for (size_t k = 0; k < sides.size(); ++k) {
+            const cuuint64_t Lk = (cuuint64_t)sides[k];
+            const cuuint64_t dims[3] = {Lk, Lk, (cuuint64_t)c->total_sites / (Lk * Lk)};
+            const cuuint64_t strides[2] = {Lk * 4, Lk * Lk * 4};  // bytes, dimensions 1 and 2
+            const cuuint32_t box[3] = {(cuuint32_t)(TX + 2 * kTmaHaloX), (cuuint32_t)(TY + 2 * kTmaHaloY), 1};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            for (int a = 0; a < kTmaArrays; ++a) {
+                void* base = a < 6 ? c->field(a / 3, a % 3) : (void*)c->cells(a - 6);
+                const CUtensorMapDataType dt =
+                    a < 6 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+                CUtensorMap* m = &maps[((size_t)sh * sides.size() + k) * kTmaArrays + a];
+                if (encode(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    return false;
+            }
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);  // the staging vector dies with this call
+    return e == cudaSuccess;
 }
 
 template <typename T>
@@ -629,21 +758,21 @@ sim_status sim_workspace_size(const sim_config* cfg, int n, const int32_t* L, si
     if (!cfg || !L || !bytes || n < 1) return SIM_EINVAL;
     std::string why;
     if (!valid_config(cfg, &why)) return SIM_EINVAL;
-    int64_t total = 0, nb = 0;
+    int64_t nb = 0;
     for (int p = 0; p < n; ++p) {
         if (L[p] < 8 || L[p] > kMaxL) return SIM_EINVAL;
         if (cfg->z_chunk > 0 && cfg->z_chunk > L[p]) return SIM_EINVAL;
         const int64_t sites = (int64_t)L[p] * L[p] * L[p];
-        total += sites;
         nb += (sites + kSitesPerBlock - 1) / kSitesPerBlock;
     }
+    const int64_t total = place_protocols(n, L, nullptr);
     if (total >= (int64_t)0xffffffffLL) return SIM_EINVAL;  // work list holds 32-bit site indices
     int64_t nt = 0;  // room for the work list of any shape the autotuner may pick
     for (int sh = 1; sh <= kNumShapes; ++sh) {
         const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
         nt = t > nt ? t : nt;
     }
-    *bytes = make_layout(*cfg, n, total, nb, nt).total;
+    *bytes = make_layout(*cfg, n, total, nb, nt, side_classes(n, L)).total;
     return SIM_OK;
 }
 
@@ -663,15 +792,21 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
     c->P.frac_cap = n * cfg->max_fractions;
     c->ws = (char*)d_workspace;
     c->stream = (cudaStream_t)cuda_stream;
-    int64_t site0 = 0;
+    std::vector<int64_t> first_site(n);
+    const int64_t site0 = place_protocols(n, L, first_site.data());
+    std::vector<int32_t> sides(L, L + n);  // tensor-map classes: the distinct sides in ascending order
+    std::sort(sides.begin(), sides.end());
+    sides.erase(std::unique(sides.begin(), sides.end()), sides.end());
+    c->n_sides = (int)sides.size();
     for (int p = 0; p < n; ++p) {
         Proto pr{};
         pr.L = L[p];
         pr.R = R[p];
-        pr.site0 = site0;
+        pr.site0 = first_site[p];
         pr.t_end = 0;
         pr.frac0 = p * cfg->max_fractions;
         pr.nfrac = 0;
+        pr.tmap = (int32_t)(std::lower_bound(sides.begin(), sides.end(), L[p]) - sides.begin());
         const int64_t sites = (int64_t)L[p] * L[p] * L[p];
         for (int64_t b = 0; b < sites; b += kSitesPerBlock) {
             Block bl{};
@@ -680,7 +815,6 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
             bl.n = (int)((sites - b) < kSitesPerBlock ? (sites - b) : kSitesPerBlock);
             c->blocks.push_back(bl);
         }
-        site0 += sites;
         c->proto.push_back(pr);
     }
     c->total_sites = site0;
@@ -707,7 +841,7 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
         const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
         nt = t > nt ? t : nt;
     }
-    c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size(), nt);
+    c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size(), nt, c->n_sides);
     c->P.n_sites = (uint64_t)site0;
     c->P.status = c->at<uint32_t>(c->lay.status);
     std::vector<int32_t> first_block(n + 1, 0);
@@ -725,6 +859,12 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
                             c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);  // host vectors may change before the copy would run
     sim_status st = cuda_check(c, e, "create copies");
+    // TMA-staged shapes: FP32 storage on the fused path, every side a multiple of 4 (16-byte row strides)
+    bool tma_fit = c->cfg.path == SIM_PATH_FUSED && c->cfg.precision == SIM_FP32;
+    for (int p = 0; p < n; ++p) tma_fit = tma_fit && L[p] % 4 == 0;
+    if (!st && tma_fit) c->tma_ok = encode_tensor_maps(c, sides);
+    if (!st && c->cfg.path == SIM_PATH_FUSED && tma_shape(c->shape) && !c->tma_ok)
+        st = fail(c, SIM_EINVAL, "tile shapes 5 and 6 need FP32 storage and lattice sides that are multiples of 4");
     if (!st) st = reset_device(c);
     if (st) {
         delete c;
@@ -938,6 +1078,7 @@ sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     int pick = c->shape;
     sim_status st = SIM_OK;
     for (int sh = 1; sh <= kNumShapes && st == SIM_OK; ++sh) {
+        if (tma_shape(sh) && !c->tma_ok) continue;
         st = set_shape(c, sh, L);
         // one untimed step (first touch), then n_steps timed plain steps
         for (int i = 0; i <= n_steps && st == SIM_OK; ++i) {
@@ -1219,7 +1360,8 @@ void sim_destroy(sim_ctx* c) {
 // that loads the library holds until the process exits.  Host code must not
 // use the array's name as a device address (on the host it is only a
 // stand-in); the real address comes from cudaGetSymbolAddress, looked up once
-// per device.
+// per device and context (a cudaDeviceReset makes a new context, whose copy of
+// the array lives elsewhere, so the cached address is looked up again).
 namespace {
 constexpr int kNoallocMaxL = 64;
 constexpr size_t kNoallocMaxSites = (size_t)kNoallocMaxL * kNoallocMaxL * kNoallocMaxL;
@@ -1233,6 +1375,25 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocFieldBy
 namespace {
 std::mutex g_noalloc_mutex;
 unsigned char* g_noalloc_base[kNoallocMaxDevices] = {};
+void* g_noalloc_ctx[kNoallocMaxDevices] = {};  // context the cached address belongs to
+
+// The calling thread's current driver context (nullptr if none or if the query
+// fails), through the runtime's driver entry point so that the library links
+// against the runtime only.
+void* current_context() {
+    using GetCurrent = int (*)(void**);
+    static GetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (GetCurrent)f;
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 // byte offsets of the launch tables behind the field buffer
 constexpr size_t kNaProto = kNoallocFieldBytes;
@@ -1253,19 +1414,26 @@ extern "C" sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t 
     if (L < 8) return SIM_EINVAL;
     if (L > kNoallocMaxL) return SIM_ENOSPC;  // the fixed scratch holds at most 64^3 sites
     if (step < 0 || step >= (int64_t)0xffffffffLL || !(dose_gy >= 0.0) || !std::isfinite(dose_gy)) return SIM_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // The launch tables are copied from host memory that lives only during this call: a captured copy node
+    // would read it after it is gone, so a call on a stream under capture is refused before any work.
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &capturing) != cudaSuccess || capturing != cudaStreamCaptureStatusNone)
+        return SIM_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return SIM_ECUDA;
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_base[dev]) {
+        void* ctx = current_context();
+        if (!g_noalloc_base[dev] || !ctx || ctx != g_noalloc_ctx[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SIM_ECUDA;
             g_noalloc_base[dev] = (unsigned char*)p;
+            g_noalloc_ctx[dev] = ctx ? ctx : current_context();  // the lookup may have created the context
         }
         base = g_noalloc_base[dev];
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     Params P = make_params(*cfg);  // frac_cap 0: the one fraction is its own quadratic partner
     const int64_t sites = (int64_t)L * L * L;
     P.n_sites = (uint64_t)sites;  // no status word here: index checks of a SIM_CHECK build skip silently
@@ -1299,15 +1467,22 @@ extern "C" sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t 
         e = cudaMemcpyAsync(buf[1][f], buf[0][f], sizeof(float) * sites, cudaMemcpyDeviceToDevice, s);
     if (e) return SIM_ECUDA;
     int cur = 0;
-    for (int sub = 0; sub < P.n_sub; ++sub) {
-        k_substep<float><<<(unsigned)blocks.size(), kThreads, 0, s>>>(
-            (const Block*)(base + kNaBlocks), (const Proto*)(base + kNaProto), (const int64_t*)(base + kNaClock), 0,
-            sub, buf[cur][0], buf[cur][1], buf[cur][2], buf[cur ^ 1][0], buf[cur ^ 1][1], buf[cur ^ 1][2], cell,
-            (const int64_t*)(base + kNaFstep), (const double*)(base + kNaFdose), (double*)(base + kNaCum), P);
+    const Block* blk = (const Block*)(base + kNaBlocks);
+    const Proto* prot = (const Proto*)(base + kNaProto);
+    const int64_t* clk = (const int64_t*)(base + kNaClock);
+    const int64_t* fst = (const int64_t*)(base + kNaFstep);
+    const double* fds = (const double*)(base + kNaFdose);
+    double* cum = (double*)(base + kNaCum);
+    int k_off = 0;
+    for (int sub = 0; sub < P.n_sub && !e; ++sub) {
+        const float *iO = buf[cur][0], *iG = buf[cur][1], *iH = buf[cur][2];
+        float *oO = buf[cur ^ 1][0], *oG = buf[cur ^ 1][1], *oH = buf[cur ^ 1][2];
+        void* args[] = {&blk, &prot, &clk, &k_off, &sub, &iO, &iG, &iH, &oO, &oG, &oH, &cell, &fst, &fds, &cum, &P};
+        // the launch's own status: an error left pending by earlier, unrelated work is neither reported nor cleared
+        e = cudaLaunchKernel((const void*)k_substep<float>, dim3((unsigned)blocks.size()), dim3(kThreads), args, 0, s);
         cur ^= 1;
     }
     for (int f = 0; f < 3 && cur == 1 && !e; ++f)  // odd n_sub: the result sits in the scratch buffer
         e = cudaMemcpyAsync(buf[0][f], buf[1][f], sizeof(float) * sites, cudaMemcpyDeviceToDevice, s);
-    if (e || cudaGetLastError() != cudaSuccess) return SIM_ECUDA;
-    return SIM_OK;
+    return e ? SIM_ECUDA : SIM_OK;
 }

@@ -62,10 +62,12 @@ __device__ __forceinline__ bool site_ok(const Params&, int64_t) { return true; }
 struct Proto {
     int32_t L;
     int32_t R;
-    int64_t site0;   // first site of this protocol in the batch arrays
+    int64_t site0;   // first site of this protocol in the batch arrays (a multiple of L^2)
     int64_t t_end;   // horizon in steps; the protocol is frozen from then on
     int32_t frac0;   // first entry in the fraction table
     int32_t nfrac;   // fractions (distinct steps)
+    int32_t tmap;    // lattice-side class: index of this side's tensor maps (TMA-staged passes)
+    int32_t pad;
 };
 
 // Work list entry: `n` consecutive sites of protocol `p` starting at local

@@ -6,6 +6,13 @@ import numpy as np
 from synth.params import P0, M
 
 FIELD_TOL = 1e-5  # per-step field tolerance, relative to the medium value of each field
+# Near-threshold decisions (oracle margin inside the field tolerance) must stay
+# below this share of all threshold decisions of a run.
+NEAR_RATIO_MAX = 1e-6
+# One flipped near-threshold decision changes at most three cell words within
+# one step: its own site, the site its division would have filled, and the
+# competing parent that wins (or loses) that site instead.
+MISMATCH_PER_NEAR = 3
 
 
 def medium(p=P0):
@@ -47,6 +54,11 @@ def random_state(L, seed, p=P0):
     return [a.astype(np.float32) for a in (O, G, H)], cell
 
 
+def near_ratio(stats):
+    """Share of the oracle's threshold decisions that fell inside the near band."""
+    return stats["n_near"] / max(1, stats["n_decisions"])
+
+
 def dilate(mask, L, hops):
     m = mask.reshape(L, L, L).copy()
     for _ in range(hops):
@@ -76,3 +88,12 @@ def compare(L, gpu_fields, gpu_cell, ora_state, near, field_tol=FIELD_TOL, hops=
     ok = dilate(near != 0, L, hops)
     return dict(field_err=max(errs), field_errs=errs, mismatch=int(diff.sum()),
                 unexplained=int((diff & ~ok).sum()), near=int(np.count_nonzero(near)))
+
+
+def assert_one_step(r):
+    """The one-step rule: fields within tolerance, every cell mismatch inside a
+    flagged neighbourhood, and no more mismatches than the flagged decisions can
+    cause."""
+    assert r["field_err"] <= FIELD_TOL, r
+    assert r["unexplained"] == 0, r
+    assert r["mismatch"] <= MISMATCH_PER_NEAR * r["near"], r

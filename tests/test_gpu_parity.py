@@ -81,8 +81,7 @@ def test_one_step_parity_ragged_batch(cuda, orc, case):
         near, stats = orc.step(p, st, SEED, i, step, dose=doses[i])
         O, G, H, gcell = sim.get_state(i)
         r = par.compare(l, (O, G, H), gcell, st, near)
-        assert r["field_err"] <= par.FIELD_TOL, (l, r)
-        assert r["unexplained"] == 0, (l, r)
+        par.assert_one_step(r)
         if doses[i] > 0:
             assert stats["n_doomed_new"] + stats["n_deaths"] > 0
     np.testing.assert_allclose(sim.delivered_dose(), doses)
@@ -100,8 +99,7 @@ def test_one_step_parity_large_lattice(cuda, orc):
     st = par.oracle_state(orc, L, fields, cell)
     near, stats = orc.step(P0, st, SEED, 0, step, dose=2.0)
     g = sim.get_state(0)
-    r = par.compare(L, g[:3], g[3], st, near)
-    assert r["field_err"] <= par.FIELD_TOL and r["unexplained"] == 0, r
+    par.assert_one_step(par.compare(L, g[:3], g[3], st, near))
     assert stats["n_divisions"] > 100
 
 
@@ -116,6 +114,7 @@ def test_run_parity_counts_and_state(cuda, orc):
     sim.load_protocols(*csr([(doses, waits)]))
     sim.run(0)
     ref = orc.run(P0, L, R, SEED, 0, doses, waits, t_end_steps=T, hours=2)
+    assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
     O, G, H, cell = sim.get_state(0)
     assert np.array_equal(cell, ref["state"].cell), ref["stats"]
     assert np.array_equal(sim.counts()[0], ref["counts"])
@@ -235,6 +234,40 @@ def test_fused_path_equals_substep_path(cuda, shape, zc):
     assert np.array_equal(out[0][2], out[1][2])
 
 
+@pytest.mark.parametrize("shape,zc,n_sub", [(5, 0, 4), (6, 0, 4), (5, 11, 4), (6, 9, 3), (5, 0, 1)])
+def test_tma_staged_path_equals_substep_path(cuda, shape, zc, n_sub):
+    """The TMA-staged passes (tile shapes 5 and 6: bulk-tensor loads of the
+    planes, threads over the level-1 region only) reproduce the substep path
+    bit for bit in FP32, with z splits, an odd substep count and passes of one
+    substep; lattice sides 24-48 (multiples of 4) so that tiles overhang the
+    lattice on every side."""
+    from paper_2303_08123_b300 import csr
+    from synth import workloads
+    L, R = [40, 24, 32, 48], [6, 5, 4, 7]
+    p = P0.replace(n_sub=n_sub)
+    prot = csr([workloads.daily_fractions(3, 2.5, 0.5), ([4.0], [0.5]), ([1.0, 3.0], [1.0, 0.5]), ([2.0], [0.0])])
+    out = []
+    for kw in (dict(path="substep"), dict(path="fused", tile_shape=shape, z_chunk=zc)):
+        sim = _sim(L, R, hours=2, t_end_steps=1500, params=p, **kw)
+        sim.load_protocols(*prot)
+        sim.run(0)
+        out.append(([sim.get_state(q) for q in range(len(L))], sim.counts(), sim.delivered_dose()))
+        sim.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_tma_shapes_need_sides_that_are_multiples_of_four(cuda):
+    from paper_2303_08123_b300 import SimError
+    with pytest.raises(SimError):
+        _sim([40, 33], [5, 4], tile_shape=5)
+    with pytest.raises(SimError):
+        _sim([40], [5], tile_shape=6, precision="bf16")
+
+
 @pytest.mark.parametrize("n_sub", [1, 3, 4])
 def test_fused_pass_split_matches_oracle(cuda, orc, n_sub):
     """n_sub split into fused passes of two (and one) substeps: one step from a
@@ -250,8 +283,7 @@ def test_fused_pass_split_matches_oracle(cuda, orc, n_sub):
     st = par.oracle_state(orc, L, fields, cell)
     near, _ = orc.step(p, st, SEED, 0, step, dose=2.0)
     g = sim.get_state(0)
-    r = par.compare(L, g[:3], g[3], st, near)
-    assert r["field_err"] <= par.FIELD_TOL and r["unexplained"] == 0, r
+    par.assert_one_step(par.compare(L, g[:3], g[3], st, near))
 
 
 def test_autotune_picks_a_shape_and_restarts_the_batch(cuda):
@@ -264,7 +296,8 @@ def test_autotune_picks_a_shape_and_restarts_the_batch(cuda):
     sim = _sim(L, R, hours=1, t_end_steps=900)
     sim.load_protocols(*prot)
     best, ms = sim.autotune(3)
-    assert best in (1, 2, 3, 4) and ms[best - 1] == ms[ms > 0].min()
+    assert best in (1, 2, 3, 4, 5, 6) and ms[best - 1] == ms[ms > 0].min()
+    assert np.all(ms > 0)  # FP32, sides multiples of 4: every shape applies, the TMA-staged ones included
     assert sim.clock()[0][0] == 0
     sim.run(0)
     for p in range(2):
@@ -287,8 +320,8 @@ def test_full_size_batch_in_bench_configuration(cuda, orc):
     for p in (0, 131, 255):
         d, w = prot[p]
         ref = orc.run(P0, 64, 8, SEED, p, d, w, t_end_steps=600, hours=1)
+        assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
         O, G, H, cell = sim.get_state(p)
-        assert ref["stats"]["n_near"] == 0 or np.array_equal(cell, ref["state"].cell)
         assert np.array_equal(cell, ref["state"].cell), (p, ref["stats"])
         for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
             assert np.max(np.abs(g - o)) / m < 1e-4
@@ -318,6 +351,7 @@ def test_ragged_batch_persistent_fused_equals_substep_and_oracle(cuda, orc):
     assert np.array_equal(out[0][2], out[1][2])
     for p in (0, 17, 39):
         ref = orc.run(P0, int(L[p]), int(R[p]), SEED, p, prot[p][0], prot[p][1], t_end_steps=1200, hours=2)
+        assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
         assert np.array_equal(out[1][0][p], ref["state"].cell), p
         assert np.array_equal(out[1][1][p], ref["counts"])
 
@@ -350,6 +384,7 @@ def test_retiring_protocols_leave_the_work_list(cuda, orc):
     assert np.array_equal(out[0][1], out[1][1])
     for p in (0, 8):  # retires mid-hour (step 900) while the others run on; the last to retire
         ref = orc.run(P0, L[p], R[p], SEED, p, prot[p][0], prot[p][1], regrowth_h=1, hours=6)
+        assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
         assert np.array_equal(out[1][0][p], ref["state"].cell), p
         assert np.array_equal(out[1][1][p], ref["counts"]), p
 
@@ -373,6 +408,7 @@ def test_incomplete_repair_parity(cuda, orc, path):
         if p is p_rep:
             for i in range(2):
                 ref = orc.run(p, L, R, SEED, i, prot[i][0], prot[i][1], t_end_steps=T, hours=3)
+                assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
                 assert np.array_equal(cells[i], ref["state"].cell), (i, ref["stats"])
                 assert np.array_equal(sim.counts()[i], ref["counts"]), i
         sim.close()
@@ -399,40 +435,60 @@ def test_physical_rate_variant(cuda, orc):
             assert np.array_equal(x, y)
     for p in range(2):
         ref = orc.run(P_PHYS, L[p], R[p], SEED, p, prot[p][0], prot[p][1], t_end_steps=T)
+        assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
         O, G, H, cell = out[1][p]
         assert np.array_equal(cell, ref["state"].cell), (p, ref["stats"])
         for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
             assert np.max(np.abs(g - o)) / m < 1e-4
 
 
-def test_single_protocol_configuration(cuda, orc):
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        return json.load(f)
+
+
+def test_single_protocol_configuration(cuda):
     """The single-protocol case (40^3, R = 5, 10 x 2 Gy at 24 h intervals, 12
-    days): the whole 288 h run on the fused hour-graph path equals the substep
-    path (all 289 hourly counts and the final state, bit for bit), and its first
-    26 hours (two fractions) equal the oracle (hourly counts and cells)."""
+    days), whole run: the fused hour-graph path equals the substep path (289
+    hourly counts and final state, bit for bit) and the oracle's own whole run
+    stored in tests/golden/single_protocol_288h.json (written from oracle/ only
+    by make_single_protocol_golden.py): all 289 hourly counts, the final cell
+    words (SHA-256), the final fields on the central plane within 1e-3 of the
+    medium value, and a near-threshold share of the oracle's decisions below
+    1e-6."""
+    import hashlib
     from paper_2303_08123_b300 import csr
     from synth import workloads
+    ref = _golden("single_protocol_288h.json")
     doses, waits = workloads.daily_fractions(10, 2.0, 24.0)
+    assert ref["doses"] == doses and ref["waits"] == waits and ref["seed"] == SEED
     T = 288 * 600
     out = []
     for path in ("fused", "substep"):
         sim = _sim([40], [5], hours=288, t_end_steps=T, path=path)
         sim.load_protocols(*csr([(doses, waits)]))
         sim.run(0)
-        out.append((sim.counts()[0], sim.get_state(0)))
+        out.append((sim.counts()[0], sim.get_state(0), sim.delivered_dose()[0]))
         sim.close()
     assert np.array_equal(out[0][0], out[1][0])
     for x, y in zip(out[0][1], out[1][1]):
         assert np.array_equal(x, y)
-    assert out[0][0][0] == 515 and np.all(out[0][0] > 0)
-    Ts = 26 * 600
-    sim = _sim([40], [5], hours=26, t_end_steps=Ts)
-    sim.load_protocols(*csr([(doses, waits)]))
-    sim.run(0)
-    ref = orc.run(P0, 40, 5, SEED, 0, doses, waits, t_end_steps=Ts, hours=26)
-    assert np.array_equal(sim.counts()[0], ref["counts"])
-    assert np.array_equal(sim.get_state(0)[3], ref["state"].cell), ref["stats"]
-    assert np.array_equal(sim.counts()[0], out[0][0][:27])
+    counts, (O, G, H, cell), dose = out[0]
+    assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
+    assert counts.tolist() == ref["counts"]
+    assert hashlib.sha256(cell.astype("<u4").tobytes()).hexdigest() == ref["final_cells_sha256"]
+    assert np.bincount(cell & 7, minlength=6).tolist() == ref["final_kind_histogram"]
+    assert dose == ref["cum_dose"] == 20.0
+    z = ref["central_plane_z"]
+    plane = slice(z * 40 * 40, (z + 1) * 40 * 40)
+    for g, name, m in zip((O, G, H), "OGH", par.medium()):
+        err = np.max(np.abs(g[plane].astype(np.float64) - np.array(ref["central_plane"][name]))) / m
+        assert err < 1e-3, (name, err)
+    sums = [float(np.sum(g.astype(np.float64))) for g in (O, G, H)]
+    for a, b, m in zip(sums, ref["field_sums"], par.medium()):
+        assert abs(a - b) / (m * 40 ** 3) < 1e-3
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
@@ -459,28 +515,62 @@ def test_two_byte_storage_same_on_every_tile_shape(cuda, precision):
 
 def test_full_size_ragged_batch_in_bench_configuration(cuda, orc):
     """The ragged bench workload at full size (1,024 protocols, radii 4-20 on
-    32^3-112^3 lattices, autotuned persistent fused path, one hour graph):
-    sampled protocols of every lattice size equal the oracle after 600 steps
-    (cells and hourly counts bit for bit, fields within 1e-4 of the medium)."""
+    32^3-112^3 lattices, autotuned persistent fused path, one hour graph): one
+    sampled protocol of every lattice side against the oracle after 600 steps,
+    then one more step of the 112^3 protocol from the GPU's own state against
+    one oracle step from that state.
+
+    Up to 80^3 the oracle's run has no near-threshold decision and the GPU run
+    equals it bit for bit (cells, hourly counts; fields within 1e-4 of the
+    medium).  The largest spheroids (R = 19-20 on 96^3 and 112^3) grow a
+    hypoxic core in their first hour: the falling O2 at the quiescence front
+    puts 1-2e-5 of that hour's decisions inside the near band, above the 1e-6
+    of the runs above.  There a cell may differ only where the oracle flagged
+    a decision during the run (2-hop neighbourhood), and the lock-step check
+    holds the GPU to the one-step rule at that size."""
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2303_08123_b300 import Simulator, csr
     from synth import workloads
     L, R, prot = workloads.ragged_batch(1024, seed=3)
     first = {}
     for p, l in enumerate(L):
         first.setdefault(int(l), p)
-    sample = [first[l] for l in sorted(first) if l <= 64]  # the oracle finishes these in seconds
+    sample = [first[l] for l in sorted(first)]  # one protocol of each side, 32^3 ... 112^3
+    assert [int(L[p]) for p in sample] == [32, 48, 64, 80, 96, 112]
     for p in sample:  # a fraction inside the hour for the sampled slots
         prot[p] = ([min(prot[p][0][0], 5.0)] + prot[p][0][1:], [0.5] + prot[p][1][1:])
+    # the oracle runs overlap the GPU run (ctypes releases the GIL)
+    pool = ThreadPoolExecutor(len(sample))
+    futs = {p: pool.submit(orc.run, P0, int(L[p]), int(R[p]), SEED, p, prot[p][0], prot[p][1], t_end_steps=600,
+                           hours=1, near=True) for p in sample}
     sim = Simulator(L, R, seed=SEED, hours=2, dose_cap_gy=30.0)
     sim.load_protocols(*csr(prot))
     sim.autotune(2)
     sim.run(600)
+    states = {p: sim.get_state(p) for p in sample}
+    counts = sim.counts()
+    big = sample[-1]
+    sim.run(1)  # one more step of the whole batch for the lock-step check
+    after = sim.get_state(big)
+    pool.shutdown()
     for p in sample:
-        d, w = prot[p]
-        ref = orc.run(P0, int(L[p]), int(R[p]), SEED, p, d, w, t_end_steps=600, hours=1)
-        O, G, H, cell = sim.get_state(p)
-        assert np.array_equal(cell, ref["state"].cell), (p, int(L[p]), ref["stats"])
-        for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
-            assert np.max(np.abs(g - o)) / m < 1e-4
-        assert np.array_equal(sim.counts()[p][:2], ref["counts"][:2])
-    assert len(sample) == 3  # lattices 32, 48 and 64
+        ref = futs[p].result()
+        l = int(L[p])
+        O, G, H, cell = states[p]
+        ratio = par.near_ratio(ref["stats"])
+        assert np.array_equal(counts[p][:2], ref["counts"][:2]), (p, l)
+        if l <= 80:
+            assert ratio < par.NEAR_RATIO_MAX, (l, ref["stats"])
+            assert np.array_equal(cell, ref["state"].cell), (p, l, ref["stats"])
+            for g, o, m in zip((O, G, H), (ref["state"].O, ref["state"].G, ref["state"].H), par.medium()):
+                assert np.max(np.abs(g - o)) / m < 1e-4
+        else:
+            assert ratio < 1e-4, (l, ref["stats"])
+            flagged = par.dilate(ref["near_any"] != 0, l, 2)
+            diff = cell != ref["state"].cell
+            assert not np.any(diff & ~flagged), (l, int(diff.sum()), int((diff & ~flagged).sum()))
+    # lock step at 112^3: the GPU's state after 600 steps, one step on both sides
+    O, G, H, cell = states[big]
+    st = par.oracle_state(orc, 112, (O, G, H), cell)
+    near, _ = orc.step(P0, st, SEED, big, 600)
+    par.assert_one_step(par.compare(112, after[:3], after[3], st, near))

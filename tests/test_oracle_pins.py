@@ -579,3 +579,71 @@ def test_run_applies_fractions_and_counts(orc):
     assert hit["cum_dose"] == 8.0 and ctrl["cum_dose"] == 0.0
     assert ctrl["steps"] == 1800 and np.all(ctrl["counts"] >= 0)
     assert hit["stats"]["n_doomed_new"] > 0
+
+
+# ----------------------------------------------------------------------------- near-threshold band
+# The parity rule of the GPU tests excuses a cell mismatch only where the oracle
+# flags a decision as near-threshold.  The band is fixed from outside the
+# oracle: the per-step field tolerance is 1e-5 of the field's medium value, and
+# an irradiation decision is near when the uniform draw lies within 1e-5 of the
+# survival probability.  A wider band would quietly excuse real GPU errors, a
+# narrower one would fail correct runs; both sides of the edge are checked.
+NEAR_BAND = 1e-5
+
+
+def _one_site_decision(orc, p, kind, O, G, H, dose=0.0, step=0, protocol=0):
+    L = 7
+    n = L ** 3
+    st = _state_from(orc, L, np.full(n, O), np.full(n, G), np.full(n, H))
+    c = 3 + L * (3 + L * 3)
+    st.cell[c] = kind | (5 << 4)
+    near, stats = orc.step(p, st, SEED, protocol, step, dose=dose)
+    assert np.count_nonzero(near[np.arange(n) != c]) == 0
+    return int(near[c]), stats, c
+
+
+@pytest.mark.parametrize("which", ["G_d", "H_d", "O_q", "G_q", "H_q"])
+@pytest.mark.parametrize("k,flagged", [(0.9, True), (-0.9, True), (1.1, False), (-1.1, False), (0.0, True)])
+def test_near_band_of_each_field_threshold(orc, which, k, flagged):
+    """A cell whose field value sits k x 1e-5 x (medium value of that field)
+    from a threshold is flagged near exactly when |k| <= 1; death thresholds
+    set the death bit (2), quiescence thresholds the quiescence bit (4)."""
+    p = P0.replace(n_sub=1, flags=F_DEATH | F_QUIESCENCE)  # fields stay as set: no diffusion, no uptake
+    H_med = 10 ** (3 - p.medium_pH)
+    theta = {"G_d": p.G_d, "H_d": 10 ** (3 - p.pH_d), "O_q": p.O_q, "G_q": p.G_q, "H_q": 10 ** (3 - p.pH_q)}[which]
+    scale = {"G_d": p.medium_G, "H_d": H_med, "O_q": p.medium_O, "G_q": p.medium_G, "H_q": H_med}[which]
+    vals = {"O": 0.2, "G": 5.0, "H": 4e-5}  # far from every threshold
+    vals[which[0]] = theta + k * NEAR_BAND * scale
+    bit = 2 if which.endswith("_d") else 4
+    flags, stats, _ = _one_site_decision(orc, p, G1, vals["O"], vals["G"], vals["H"])
+    assert bool(flags & bit) == flagged, (which, k, flags)
+    assert flags & ~bit == 0
+    assert stats["n_near"] == int(flagged)
+    assert stats["n_decisions"] == (1 if (which.endswith("_d") and vals["G"] < p.G_d or
+                                          which.endswith("_d") and vals["H"] > 10 ** (3 - p.pH_d)) else 2)
+
+
+@pytest.mark.parametrize("k,flagged", [(0.5, True), (-0.5, True), (2.0, False), (-2.0, False)])
+def test_near_band_of_the_irradiation_draw(orc, k, flagged):
+    """The dose is solved so that the survival probability S of one oxic G1
+    cell lies k x 1e-5 from its Philox draw u: flagged (bit 1) exactly when
+    |u - S| <= 1e-5, and the cell is doomed exactly when u >= S."""
+    p = P0.replace(n_sub=1, flags=0)
+    L, protocol = 7, 5
+    c = 3 + L * (3 + L * 3)
+    for step in range(4321, 4421):  # the first step whose draw lies well inside (0, 1)
+        u = float(orc.philox(np.array([[c, step, 1, protocol]], dtype=np.uint32), SEED)[0, 0] >> 8) / 2 ** 24
+        if 0.2 < u < 0.8:
+            break
+    assert 0.2 < u < 0.8
+    S_target = u + k * NEAR_BAND
+    O = p.medium_O
+    mod = p.phi[0] * (p.omf_m * O + p.omf_K) / (p.omf_m * (O + p.omf_K))
+    a, b = p.alpha * mod, p.beta * mod * mod
+    D = (-a + math.sqrt(a * a - 4 * b * math.log(S_target))) / (2 * b)  # b D^2 + a D + ln S = 0
+    assert math.isclose(_lq_survival(p, G1, O, D), S_target, rel_tol=0, abs_tol=1e-12)
+    flags, stats, c2 = _one_site_decision(orc, p, G1, O, 5.0, 4e-5, dose=D, step=step, protocol=protocol)
+    assert c2 == c
+    assert bool(flags & 1) == flagged and flags & ~1 == 0, (k, flags)
+    assert stats["n_near"] == int(flagged) and stats["n_decisions"] == 1
+    assert stats["n_doomed_new"] == int(u >= S_target)

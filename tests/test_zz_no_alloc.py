@@ -32,16 +32,20 @@ def cuda():
     return torch
 
 
-def test_noalloc_diffusion_matches_context_path_twice(cuda):
+# (lattice side, substeps per step): the default case; an odd substep count,
+# whose result the entry point copies back from its scratch array; and the
+# largest lattice, which fills the scratch array's field part exactly
+@pytest.mark.parametrize("L,n_sub", [(40, 4), (24, 3), (64, 4)])
+def test_noalloc_diffusion_matches_context_path_twice(cuda, L, n_sub):
     torch = cuda
     from paper_2303_08123_b300 import Simulator, csr
     from paper_2303_08123_b300.sim import load_library, make_config
 
     lib = load_library()
-    L, seed, step, dose = 40, 0x5EED_00A1, 1500, 2.0
+    seed, step, dose = 0x5EED_00A1, 1500, 2.0
     # only the fields and the irradiation marks change: phases are long enough
     # that no cell changes kind within two steps, and cell events are off
-    p = P0.replace(dur_h=(1000.0, 1000.0, 1000.0, 1000.0), flags=F_REACTION | F_DIFFUSION)
+    p = P0.replace(dur_h=(1000.0, 1000.0, 1000.0, 1000.0), flags=F_REACTION | F_DIFFUSION, n_sub=n_sub)
     fields, cell = par.random_state(L, 21, p)
     ages = np.random.default_rng(22).integers(0, 1000, L ** 3).astype(np.uint32)
     cell = np.where(cell & 7, (cell & 0xF) | (ages << 4), 0).astype(np.uint32)
@@ -91,3 +95,25 @@ def test_noalloc_rejects_lattices_beyond_its_scratch(cuda):
     bad = make_config(P0, precision="bf16")
     assert lib.sim_diffuse_noalloc(ctypes.byref(bad), 16, 0, 0.0, *(ctypes.c_void_p(t.data_ptr()) for t in bufs),
                                    ctypes.c_void_p(cell.data_ptr()), None) == -1
+
+
+def test_noalloc_refuses_a_stream_under_capture(cuda):
+    """The launch tables come from host memory that lives only during the call,
+    so a call on a stream that is being captured is refused before any work."""
+    torch = cuda
+    from paper_2303_08123_b300.sim import load_library, make_config
+
+    lib = load_library()
+    cfg = make_config(P0)
+    L = 16
+    bufs = [torch.full((L ** 3,), 0.25, dtype=torch.float32, device="cuda") for _ in range(3)]
+    cell = torch.zeros(L ** 3, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        st = lib.sim_diffuse_noalloc(ctypes.byref(cfg), L, 0, 0.0, *(ctypes.c_void_p(t.data_ptr()) for t in bufs),
+                                     ctypes.c_void_p(cell.data_ptr()), ctypes.c_void_p(side.cuda_stream))
+        bufs[0].add_(0.0)  # keeps the captured graph non-empty
+    assert st == -1
+    torch.cuda.synchronize()
+    assert float(bufs[1].min()) == 0.25 and float(bufs[1].max()) == 0.25  # nothing was enqueued
