@@ -320,7 +320,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     if args.full_run:
         return full_run(args, sim, prot, mean_h, Ls, shape, shape_ms, world, rank, dev, barrier)
-    sim.run(STEPS_PER_HOUR * (start_h - W))  # untimed advance to the warm-up hours
+    if start_h > W:  # untimed advance to the warm-up hours (sim.run(0) would run to every horizon)
+        sim.run(STEPS_PER_HOUR * (start_h - W))
     for _ in range(W):
         sim.run(STEPS_PER_HOUR)
     barrier()

@@ -137,6 +137,21 @@ __device__ __forceinline__ uint32_t dither_bits(uint32_t site, uint32_t step, ui
     return x;
 }
 
+// The rounding bits of one site's three fields from one hash: each stored
+// value needs 16 random bits (the rounding probability resolved to 2^-16), so
+// O2 takes the low and glucose the high half of the hash, and H+ the low half
+// of one more xor-shift-multiply round of it.
+struct Dither3 {
+    uint32_t o, g, h;
+};
+__device__ __forceinline__ Dither3 dither3(uint32_t site, uint32_t step, uint32_t salt) {
+    const uint32_t x = dither_bits(site, step, salt);
+    uint32_t y = x ^ (x >> 15);
+    y *= 0x2C1B3C6Du;
+    y ^= y >> 12;
+    return {x & 0xFFFFu, x >> 16, y & 0xFFFFu};
+}
+
 template <typename T>
 __device__ __forceinline__ T cvt_sr(float v, uint32_t r);
 template <>
@@ -153,8 +168,9 @@ __device__ __forceinline__ __half cvt_sr<__half>(float v, uint32_t r) {
     const __half lo = __float2half_rd(v), hi = __float2half_ru(v);
     const float flo = __half2float(lo), fhi = __half2float(hi);
     if (fhi == flo) return lo;
-    const float u = (float)(r >> 8) * 0x1p-24f;  // uniform in [0, 1)
-    return (u < (v - flo) / (fhi - flo)) ? hi : lo;
+    const float u = (float)(r & 0xFFFFu) * 0x1p-16f;  // uniform in [0, 1) from the 16 rounding bits
+    // fhi - flo is one FP16 spacing, a power of two: its reciprocal and the product are exact
+    return (u < (v - flo) * __frcp_rn(fhi - flo)) ? hi : lo;
 }
 
 __device__ __forceinline__ bool is_face(int L, int x, int y, int z) {

@@ -354,17 +354,15 @@ __global__ void __launch_bounds__(FusedShape<TX, TY, K>::THREADS, SIM_FUSED_MIN_
                     const bool sa = oa && !fa && !zface, sb = ob && !fb && !zface;  // interior sites written
                     const bool vw = vec && sa && sb;
                     if (sa || sb) {
-                        // stochastic-rounding bits per (site, step, pass, field); the substep path uses
-                        // salts 3 * substep + field, a fused pass 3 * (its last substep) + field
+                        // stochastic-rounding bits per (site, step, pass): one hash per site serves its
+                        // three fields; the substep path salts with the substep, a fused pass with
+                        // 100 + its last substep
                         uint32_t r[6] = {0, 0, 0, 0, 0, 0};
                         if constexpr (sizeof(T) != 4) {
                             const uint32_t ga = (uint32_t)(pr.site0 + col + o), stp = (uint32_t)step;
-                            const uint32_t salt = 3u * (EPI ? (uint32_t)P.n_sub - 1u : (uint32_t)K - 1u) + 100u;
-#pragma unroll
-                            for (int f = 0; f < 3; ++f) {
-                                r[2 * f] = dither_bits(ga, stp, salt + f);
-                                r[2 * f + 1] = dither_bits(ga + 1, stp, salt + f);
-                            }
+                            const uint32_t salt = (EPI ? (uint32_t)P.n_sub - 1u : (uint32_t)K - 1u) + 100u;
+                            const Dither3 da = dither3(ga, stp, salt), db = dither3(ga + 1, stp, salt);
+                            r[0] = da.o, r[1] = db.o, r[2] = da.g, r[3] = db.g, r[4] = da.h, r[5] = db.h;
                         }
                         st_pair(oO + pr.site0 + col + o, v[0], vw, sa, sb, r[0], r[1]);
                         st_pair(oG + pr.site0 + col + o, v[1], vw, sa, sb, r[2], r[3]);

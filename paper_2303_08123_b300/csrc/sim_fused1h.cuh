@@ -13,7 +13,7 @@
 //   * stage values are widened to FP32 when read; computed levels stay FP32 in
 //     shared memory;
 //   * every stored field value rounds stochastically with the bits of the same
-//     counter-based hash (site, step, pass salt, field) as the column-pair
+//     counter-based hash (site, step, pass salt; one hash per site) as the column-pair
 //     kernel, so both kernels give bit-identical results.
 #pragma once
 #include "sim_fused.cuh"
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     const uint32_t lane = threadIdx.x & 31u;
     const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
     // stochastic-rounding salt of this pass, as in the column-pair kernel
-    const uint32_t salt = 3u * (EPI ? (uint32_t)P.n_sub - 1u : (uint32_t)K - 1u) + 100u;
+    const uint32_t salt = (EPI ? (uint32_t)P.n_sub - 1u : (uint32_t)K - 1u) + 100u;
 
     const int64_t step = *clock + k_off;
     uint32_t* cnt = icount + (step & 1);
@@ -238,10 +238,10 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                 if (outc && (!CHK || (q >= z0 && q < z1)) && site_ok(P, pr.site0 + col + o)) {
                     const bool face = fxy || (CHK && (q == 0 || q == L - 1));
                     if (!face) {
-                        const uint32_t gs = (uint32_t)(pr.site0 + col + o), stp = (uint32_t)step;
-                        d0[o] = cvt_sr<T>(vog.x, dither_bits(gs, stp, salt));
-                        d1[o] = cvt_sr<T>(vog.y, dither_bits(gs, stp, salt + 1u));
-                        d2[o] = cvt_sr<T>(vh, dither_bits(gs, stp, salt + 2u));
+                        const Dither3 r = dither3((uint32_t)(pr.site0 + col + o), (uint32_t)step, salt);
+                        d0[o] = cvt_sr<T>(vog.x, r.o);
+                        d1[o] = cvt_sr<T>(vog.y, r.g);
+                        d2[o] = cvt_sr<T>(vh, r.h);
                     }
                     const uint32_t w0 = wr[sq];
                     if (EPI) dC[o] = face ? w0 : update_cell(w0, vog.x, vog.y, vh, P, want);

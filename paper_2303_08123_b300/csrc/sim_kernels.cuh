@@ -121,12 +121,11 @@ __global__ void __launch_bounds__(kThreads) k_substep(const Block* __restrict__ 
         // an immediately killed one (variant switch) does not
         const uint32_t kr = w & kKindMask;
         if (react && kr != kEmpty) uptake(kr, O, Gv, P, uO, uG, pH);
-        // stochastic-rounding bits per (site, step, substep, field); unused with FP32 storage
-        const bool sr = sizeof(T) != 4;
-        const uint32_t salt = 3u * (uint32_t)sub;
-        oO[g] = cvt_sr<T>(fmaxf(__fsub_rn(tO, uO), 0.f), sr ? dither_bits((uint32_t)g, (uint32_t)step, salt) : 0u);
-        oG[g] = cvt_sr<T>(fmaxf(__fsub_rn(tG, uG), 0.f), sr ? dither_bits((uint32_t)g, (uint32_t)step, salt + 1) : 0u);
-        oH[g] = cvt_sr<T>(fmaxf(__fadd_rn(tH, pH), 0.f), sr ? dither_bits((uint32_t)g, (uint32_t)step, salt + 2) : 0u);
+        // stochastic-rounding bits per (site, step, substep), one hash for the three fields; unused with FP32
+        const Dither3 r = sizeof(T) != 4 ? dither3((uint32_t)g, (uint32_t)step, (uint32_t)sub) : Dither3{0u, 0u, 0u};
+        oO[g] = cvt_sr<T>(fmaxf(__fsub_rn(tO, uO), 0.f), r.o);
+        oG[g] = cvt_sr<T>(fmaxf(__fsub_rn(tG, uG), 0.f), r.g);
+        oH[g] = cvt_sr<T>(fmaxf(__fadd_rn(tH, pH), 0.f), r.h);
     }
 }
 

@@ -108,6 +108,50 @@ def run_ga(setup: SimSetup, cfg: ga.GAConfig, generations: int, rng, net: Surrog
     return history
 
 
+def simulations_to_equal_best(plain_hist, screened_hist, training: int):
+    """Full simulations each arm spent until its best-so-far count first reached
+    the best count the plain GA reaches by its last generation; the screened
+    arm's training simulations are counted.  Returns (target count, plain
+    simulations, screened simulations or None if it never got there)."""
+    def first(hist, target, extra):
+        best = float("inf")
+        for count, used in hist:
+            best = min(best, count)
+            if best <= target:
+                return used + extra
+        return None
+    target = min(c for c, _ in plain_hist)
+    return target, first(plain_hist, target, 0), first(screened_hist, target, training)
+
+
+def compare_arms(setup: SimSetup, cfg: ga.GAConfig, generations: int, plain_population: int,
+                 simulated: int, pool: int, train: int, seed: int, epochs: int = 60, log_dir: str = ""):
+    """The plain GA (plain_population children simulated per generation) against
+    the screened GA (pool candidates per generation, the surrogate's best
+    `simulated` of them simulated), the surrogate trained first on `train`
+    simulated random protocols.  Returns a dict with both histories (best count,
+    cumulative simulations per generation) and simulations_to_equal_best."""
+    rng = np.random.default_rng(seed)
+    train_set = [ga.to_pairs(ga.random_protocol(cfg, rng)) for _ in range(train)]
+    y = simulate(train_set, setup, seed_offset=10_000)
+    net = Surrogate(batch_max=max(4096, pool), seed=seed)
+    fit_surrogate(net, features(train_set), y, epochs=epochs)
+    out = {}
+    for arm, population, kw in (("plain", plain_population, {}),
+                                ("screened", simulated, {"net": net, "pool": pool})):
+        log = open(f"{log_dir}/ga_{arm}.jsonl", "w") if log_dir else None
+        hist = run_ga(setup, dataclasses.replace(cfg, population=population), generations,
+                      np.random.default_rng(seed + 1), log=log, **kw)
+        if log:
+            log.close()
+        out[arm] = hist
+    net.close()
+    out["training_simulations"] = train
+    out["target"], out["plain_sims_to_best"], out["screened_sims_to_best"] = \
+        simulations_to_equal_best(out["plain"], out["screened"], train)
+    return out
+
+
 def main():
     """Screened vs unscreened GA on small lattices: best final count reached
     against the number of full simulations spent (one JSON line per arm)."""
@@ -121,7 +165,29 @@ def main():
     ap.add_argument("--pool", type=int, default=2048)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--log", default="", help="directory for one JSONL file per arm (generation by generation)")
+    ap.add_argument("--compare", action="store_true",
+                    help="simulations-to-equal-best: plain GA of --plain-population against the screened GA "
+                         "simulating --simulated of --pool candidates per generation")
+    ap.add_argument("--plain-population", type=int, default=4096)
+    ap.add_argument("--simulated", type=int, default=512)
+    ap.add_argument("--L", type=int, default=24)
+    ap.add_argument("--R", type=int, default=5)
     a = ap.parse_args()
+    if a.compare:
+        setup = SimSetup(L=a.L, R=a.R, regrowth_h=6)
+        cfg = ga.GAConfig(n_slots=48, d_max=2.5, total_cap=8.0, min_gap=4,
+                          mutations=("swap", "split", "dose_time", "dose_value"), p_mut=0.5)
+        r = compare_arms(setup, cfg, a.generations, a.plain_population, a.simulated, a.pool, a.train, a.seed,
+                         log_dir=a.log)
+        print(json.dumps({"lattice": a.L, "radius": a.R, "generations": a.generations,
+                          "plain_population": a.plain_population, "pool": a.pool, "simulated": a.simulated,
+                          "training_simulations": a.train, "target_count": r["target"],
+                          "plain_sims_to_best": r["plain_sims_to_best"],
+                          "screened_sims_to_best": r["screened_sims_to_best"],
+                          "plain_best": [h[0] for h in r["plain"]], "screened_best": [h[0] for h in r["screened"]],
+                          "plain_sims": [h[1] for h in r["plain"]],
+                          "screened_sims": [h[1] + a.train for h in r["screened"]]}))
+        return
     setup = SimSetup(L=24, R=5, regrowth_h=6)
     cfg = ga.GAConfig(n_slots=48, d_max=2.5, total_cap=8.0, min_gap=4, population=a.population,
                       mutations=("swap", "split", "dose_time", "dose_value"), p_mut=0.5)

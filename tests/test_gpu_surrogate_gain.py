@@ -61,3 +61,22 @@ def test_surrogate_promotes_better_protocols_than_random(cuda):
     assert yp.mean() < yr.mean() and t.pvalue < 1e-6, (yp.mean(), yr.mean(), t.pvalue)
     # the promoted set's best equals what random sampling needs many more simulations to reach
     assert yp.min() <= np.sort(yr)[2]
+
+
+def test_screened_ga_reaches_the_plain_best_with_fewer_simulations(cuda):
+    """Equal best fitness with fewer full simulations, training included: the
+    plain GA simulates 256 children per generation for 10 generations; the
+    screened GA ranks 2,048 candidates per generation with a surrogate trained
+    on 1,024 simulated random protocols and simulates the best 128.  The
+    screened arm's simulations until its best-so-far count first reaches the
+    plain GA's final best (its 1,024 training simulations counted) must be
+    fewer than the plain GA's own."""
+    from paper_2303_08123_b300 import ga
+    from paper_2303_08123_b300.screen import SimSetup, compare_arms
+    setup = SimSetup(L=24, R=5, regrowth_h=6)
+    cfg = ga.GAConfig(n_slots=48, d_max=2.5, total_cap=8.0, min_gap=4,
+                      mutations=("swap", "split", "dose_time", "dose_value"), p_mut=0.5)
+    r = compare_arms(setup, cfg, generations=10, plain_population=256, simulated=128, pool=2048, train=1024, seed=5)
+    assert r["screened_sims_to_best"] is not None, r
+    assert r["screened_sims_to_best"] < r["plain_sims_to_best"], (r["target"], r["plain_sims_to_best"],
+                                                                  r["screened_sims_to_best"])
