@@ -234,10 +234,13 @@ def precision_error(precision, n, steps):
     Lq, Rq, seed = 64, 8, 0x5EED_0004
     prot = [(dd, [0.5] + ww[1:]) for dd, ww in workloads.ga_batch(n, seed=4)]
     off, d, w = csr(prot)
+    from concurrent.futures import ThreadPoolExecutor
     ref = oracle.run_batch(PARAMS, [Lq] * n, [Rq] * n, seed, off, d, w, t_end_steps=steps)
     sample = list(range(0, n, max(1, n // 4)))
-    ref_state = {p: oracle.run(PARAMS, Lq, Rq, seed, p, prot[p][0], prot[p][1], t_end_steps=steps)["state"]
-                 for p in sample}
+    with ThreadPoolExecutor(len(sample)) as ex:  # the oracle's ctypes calls release the GIL
+        futs = {p: ex.submit(oracle.run, PARAMS, Lq, Rq, seed, p, prot[p][0], prot[p][1], t_end_steps=steps)
+                for p in sample}
+        ref_state = {p: f.result()["state"] for p, f in futs.items()}
     med = np.array([PARAMS.medium_O, PARAMS.medium_G, 10 ** (3 - PARAMS.medium_pH)])
     sim = Simulator([Lq] * n, [Rq] * n, seed=seed, precision=precision, t_end_steps=steps, dose_cap_gy=20.0,
                     params=PARAMS)
@@ -424,7 +427,7 @@ def run_ours(args):
                                               "and the re-seeding inside the timed region)"},
                 "gpu_launches": launches_per_step * K,
                 "clocks": clk.summary()}
-        if args.precision != "fp32":
+        if args.precision != "fp32" or args.error_vs_oracle:
             line["error_vs_oracle"] = precision_error(args.precision, args.error_sample, args.error_steps)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(mean_h)
@@ -493,6 +496,8 @@ def main():
                          "single: one protocol on 40^3 for 288 h")
     ap.add_argument("--start-hour", type=int, default=None,
                     help="simulated hour at which the timed window opens (default 24; 0 for --workload single)")
+    ap.add_argument("--error-vs-oracle", action="store_true",
+                    help="report error_vs_oracle for FP32 storage too (always reported for BF16 / FP16)")
     ap.add_argument("--error-sample", type=int, default=8,
                     help="2-byte storage: protocols checked against the oracle for error_vs_oracle")
     ap.add_argument("--error-steps", type=int, default=1200,

@@ -87,11 +87,10 @@ typedef struct {
     int32_t path;           /* SIM_PATH_FUSED (default) or SIM_PATH_SUBSTEP */
     int32_t tile_shape;     /* fused tile: 0 auto; 1 = 32 x 16, 2 = 16 x 16 with two columns per
                                thread (packed FP32); 3 = 32 x 16, 4 = 16 x 16 with one column per
-                               thread; with the planes staged by TMA (FP32 storage, every lattice
-                               side a multiple of 4): 5 = 32 x 16, 6 = 16 x 16 with one column per
-                               thread, 7 = 32 x 32, 8 = 32 x 16 with two columns per thread.  For
-                               a given storage precision every shape gives the same results bit
-                               for bit */
+                               thread; 5 = 32 x 16, 6 = 16 x 16 with one column per thread and the
+                               planes staged by TMA (FP32 storage, every lattice side a multiple of
+                               4).  For a given storage precision every shape gives the same
+                               results bit for bit */
     int32_t z_chunk;        /* fused z range per CTA: 0 auto, else planes per CTA */
 } sim_config;
 
@@ -262,10 +261,10 @@ sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, doubl
 
 /*
  * Autotuner of the fused path: time n_steps plain steps of this context's own
- * batch with every applicable tile shape (sim_config.tile_shape 1..8), keep the
+ * batch with every applicable tile shape (sim_config.tile_shape 1..6), keep the
  * fastest, then re-seed every spheroid and set the clock to 0 (call it right
  * after sim_load_protocols).  *best (may be NULL) receives the chosen shape
- * (0 on the substep path); ms (8 entries, may be NULL) the device milliseconds
+ * (0 on the substep path); ms (6 entries, may be NULL) the device milliseconds
  * per step of each shape, -1 where a shape does not apply.  Synchronises.
  */
 sim_status sim_autotune(sim_ctx* ctx, int n_steps, int* best, double* ms);

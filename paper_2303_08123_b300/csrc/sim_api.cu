@@ -39,7 +39,7 @@ struct Layout {
         clock, status, final_count, first_block, part64, part32, tot64, tot32, tile_ctr, tmaps, total;
 };
 
-constexpr int kTmaShapes = 4;  // tile shapes 5-8 stage their planes by TMA (one set of tensor maps each)
+constexpr int kTmaShapes = 2;  // tile shapes 5 and 6 stage their planes by TMA (one set of tensor maps each)
 
 // Number of distinct lattice sides (one set of tensor maps each).
 int side_classes(int n, const int32_t* L) {
@@ -105,19 +105,17 @@ bool valid_config(const sim_config* cfg, std::string* why) {
         return *why = "repair_half_h must be finite and >= 0", false;
     if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
     if (cfg->path < SIM_PATH_FUSED || cfg->path > SIM_PATH_SUBSTEP) return *why = "unknown kernel path", false;
-    if (cfg->tile_shape < 0 || cfg->tile_shape > 8) return *why = "tile_shape must be in 0..8", false;
+    if (cfg->tile_shape < 0 || cfg->tile_shape > 6) return *why = "tile_shape must be in 0..6", false;
     if (cfg->z_chunk < 0) return *why = "z_chunk must be >= 0", false;
     return true;
 }
 
 // Tile shapes of the fused kernels: (x extent, y extent); shapes 1-2 run two
-// columns per thread (packed f32x2), shapes 3-4 one column per thread; with the
-// planes staged by TMA (FP32 storage): shapes 5-6 one column per thread, shapes
-// 7-8 two columns per thread.
-constexpr int kNumShapes = 8;
-constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0},   {32, 16}, {16, 16}, {32, 16}, {16, 16},
-                                                {32, 16}, {16, 16}, {32, 32}, {32, 16}};
-bool tma_shape(int sh) { return sh >= 5 && sh <= 8; }
+// columns per thread (packed f32x2), shapes 3-4 one column per thread, shapes
+// 5-6 one column per thread with the planes staged by TMA (FP32 storage).
+constexpr int kNumShapes = 6;
+constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0}, {32, 16}, {16, 16}, {32, 16}, {16, 16}, {32, 16}, {16, 16}};
+bool tma_shape(int sh) { return sh == 5 || sh == 6; }
 
 // First site of each protocol: the running total rounded up to a multiple of
 // L^2, so that a protocol's planes are whole z-slices of the L x L x Z volume a
@@ -375,23 +373,6 @@ void launch_tma_f(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, int
         (int)c->tiles.size(), pass, c->P);
 }
 
-template <int TX, int TY, int K, bool EPI, bool FULL>
-void launch_tma2_f(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, int cbuf, uint32_t* cout, int pass) {
-    using Sh = Tma2Shape<TX, TY, K>;
-    constexpr auto kern = k_tma2<TX, TY, K, EPI, FULL>;
-    static unsigned grid = 0;
-    if (!grid) grid = persistent_grid(kern, Sh::THREADS, tma2_smem_bytes<TX, TY, K>(), ~0ull);
-    const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
-    const CUtensorMap* maps =
-        c->at<CUtensorMap>(c->lay.tmaps) + (size_t)(c->shape - 5) * c->n_sides * kTmaArrays;
-    kern<<<g, Sh::THREADS, tma2_smem_bytes<TX, TY, K>(), s>>>(
-        c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first, maps,
-        3 * buf, (float*)c->field(buf ^ 1, 0), (float*)c->field(buf ^ 1, 1), (float*)c->field(buf ^ 1, 2), 6 + cbuf,
-        cout, c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
-        c->at<uint32_t>(c->lay.intents), c->at<uint32_t>(c->lay.icount), c->at<uint32_t>(c->lay.tile_ctr),
-        (int)c->tiles.size(), pass, c->P);
-}
-
 template <int TX, int TY, int K, bool EPI>
 void launch_tma_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
                   int pass) {
@@ -402,24 +383,12 @@ void launch_tma_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, con
         launch_tma_f<TX, TY, K, EPI, false>(c, s, k_off, first, buf, cbuf, cout, pass);
 }
 
-template <int TX, int TY, int K, bool EPI>
-void launch_tma2_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
-                   int pass) {
-    const int cbuf = cin == c->cells(0) ? 0 : 1;
-    if ((c->P.flags & (kFDiffusion | kFReaction)) == (kFDiffusion | kFReaction))
-        launch_tma2_f<TX, TY, K, EPI, true>(c, s, k_off, first, buf, cbuf, cout, pass);
-    else
-        launch_tma2_f<TX, TY, K, EPI, false>(c, s, k_off, first, buf, cbuf, cout, pass);
-}
-
 template <typename T, int K, bool EPI>
 void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
                     int pass) {
     if constexpr (std::is_same<T, float>::value) {  // TMA staging: FP32 storage only
         if (c->shape == 5) return launch_tma_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
         if (c->shape == 6) return launch_tma_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
-        if (c->shape == 7) return launch_tma2_t<32, 32, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
-        if (c->shape == 8) return launch_tma2_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     }
     if (c->shape == 3) return launch_fused1_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     if (c->shape == 4) return launch_fused1_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
@@ -486,25 +455,6 @@ cudaError_t tma_attrs_shape() {
     return e;
 }
 
-template <int TX, int TY, int K, bool FULL>
-cudaError_t tma2_attrs_k() {
-    cudaError_t e = cudaFuncSetAttribute(k_tma2<TX, TY, K, false, FULL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma2_smem_bytes<TX, TY, K>());
-    if (!e)
-        e = cudaFuncSetAttribute(k_tma2<TX, TY, K, true, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma2_smem_bytes<TX, TY, K>());
-    return e;
-}
-
-template <int TX, int TY>
-cudaError_t tma2_attrs_shape() {
-    cudaError_t e = tma2_attrs_k<TX, TY, 1, true>();
-    if (!e) e = tma2_attrs_k<TX, TY, 2, true>();
-    if (!e) e = tma2_attrs_k<TX, TY, 1, false>();
-    if (!e) e = tma2_attrs_k<TX, TY, 2, false>();
-    return e;
-}
-
 template <typename T>
 cudaError_t fused_attrs() {
     cudaError_t e = fused_attrs_shape<T, 32, 16>();
@@ -514,8 +464,6 @@ cudaError_t fused_attrs() {
     if constexpr (std::is_same<T, float>::value) {
         if (!e) e = tma_attrs_shape<32, 16>();
         if (!e) e = tma_attrs_shape<16, 16>();
-        if (!e) e = tma2_attrs_shape<32, 32>();
-        if (!e) e = tma2_attrs_shape<32, 16>();
     }
     return e;
 }
@@ -915,8 +863,10 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
     bool tma_fit = c->cfg.path == SIM_PATH_FUSED && c->cfg.precision == SIM_FP32;
     for (int p = 0; p < n; ++p) tma_fit = tma_fit && L[p] % 4 == 0;
     if (!st && tma_fit) c->tma_ok = encode_tensor_maps(c, sides);
+    // without the autotuner a 16 x 16 one-column context runs the TMA-staged kernel of the same tiles
+    if (!st && cfg->tile_shape == 0 && c->tma_ok && c->shape == 4) c->shape = 6;
     if (!st && c->cfg.path == SIM_PATH_FUSED && tma_shape(c->shape) && !c->tma_ok)
-        st = fail(c, SIM_EINVAL, "tile shapes 5-8 need FP32 storage and lattice sides that are multiples of 4");
+        st = fail(c, SIM_EINVAL, "tile shapes 5 and 6 need FP32 storage and lattice sides that are multiples of 4");
     if (!st) st = reset_device(c);
     if (st) {
         delete c;

@@ -372,352 +372,4 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
 }
 
 
-// ---------------------------------------------------------------------------
-// Column pairs on TMA-staged planes.  The same pass with every thread owning
-// two adjacent columns (a, b) = (x, x + 1), x even, of the level-1 region and
-// computing both with packed f32x2 arithmetic, field by field: stencils,
-// uptake (an empty site consumes with weight 0, which gives exact zeros) and
-// the clamp-free parts of the update.  The level-1 region is widened to an even
-// number of columns (two beyond the tile on each side), so the pair's centre
-// and its y neighbours are single 8-byte shared-memory loads of the planar
-// staged arrays; the outer x neighbours (x - 1, x + 2) are 4-byte loads.  With
-// a 32 x 32 tile a CTA holds 640 threads and the whole pass needs 1.25 thread
-// lanes per output site.  Per lane the operation sequence is the pinned one of
-// stencil_t and uptake, so the results equal the other paths bit for bit.
-template <int TX, int TY, int K>
-struct Tma2Shape {
-    static constexpr int BX = TX + 2 * kTmaHaloX;  // staged box (x extent)
-    static constexpr int BY = TY + 2 * kTmaHaloY;  // staged box (y extent)
-    static constexpr int NB = BX * BY;
-    static constexpr int XL = (K > 1) ? 2 : 0;     // columns of the level-1 region on each side of the tile
-    static constexpr int RX = TX + 2 * XL, RY = TY + 2 * (K - 1);
-    static constexpr int PX = RX / 2, NP = PX * RY;  // column pairs of the level-1 region
-    static constexpr int THREADS = (NP + 31) / 32 * 32;
-    static_assert((NB * 4) % 128 == 0, "every staged array must start 128-byte aligned");
-    static_assert(TX % 2 == 0 && BX % 2 == 0, "pairs start on even columns");
-    static_assert(K >= 1 && K <= kTmaHaloY, "the box carries a halo of at most two rows");
-};
-
-template <int TX, int TY, int K>
-constexpr size_t tma2_smem_bytes() {
-    using S = Tma2Shape<TX, TY, K>;
-    return 128 + (size_t)kTmaStages * 4 * S::NB * sizeof(float) +
-           (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::NP * sizeof(float2);
-}
-
-// uptake of one substep for a column pair, lane by lane the pinned sequence of
-// `uptake`; an empty lane has consumption weight 0 and gets exact zeros
-__device__ __forceinline__ void uptake2(uint32_t ka, uint32_t kb, float2 O, float2 Gv, const Params& P, float2& uO,
-                                        float2& uG, float2& pH) {
-    const float2 f = f2(ka == kEmpty ? 0.f : (ka == kQ ? P.f_Q : 1.f), kb == kEmpty ? 0.f : (kb == kQ ? P.f_Q : 1.f));
-    const float2 a = __fadd2_rn(O, f2(P.K_O, P.K_O)), b = __fadd2_rn(O, f2(P.O_an, P.O_an));
-    const float2 c = __fadd2_rn(Gv, f2(P.K_G, P.K_G));
-    const float2 ab = __fmul2_rn(a, b);
-    const float2 abc = __fmul2_rn(ab, c);
-    const float2 r = f2(__fdividef(1.f, abc.x), __fdividef(1.f, abc.y));
-    uO = __fmul2_rn(__fmul2_rn(__fmul2_rn(f, f2(P.q_O, P.q_O)), O), __fmul2_rn(__fmul2_rn(b, c), r));
-    const float2 gg = __fmul2_rn(__fmul2_rn(__fmul2_rn(f, f2(P.q_G, P.q_G)), Gv), __fmul2_rn(ab, r));
-    const float2 wa = __fmul2_rn(f2(P.O_an, P.O_an), __fmul2_rn(__fmul2_rn(a, c), r));
-    const float km1 = __fsub_rn(P.k_an, 1.f);
-    uG = __fmul2_rn(gg, __ffma2_rn(f2(km1, km1), wa, f2(1.f, 1.f)));
-    pH = __fmul2_rn(__fmul2_rn(__fmul2_rn(f2(P.q_H, P.q_H), gg), f2(P.k_an, P.k_an)), wa);
-}
-
-template <int TX, int TY, int K, bool EPI, bool FULL>
-__global__ void __launch_bounds__(Tma2Shape<TX, TY, K>::THREADS, 1)
-    k_tma2(const Tile* __restrict__ tiles, const Proto* __restrict__ protos, const int64_t* __restrict__ clock,
-           int k_off, int first, const CUtensorMap* __restrict__ maps, int map_in, float* __restrict__ oO,
-           float* __restrict__ oG, float* __restrict__ oH, int map_cin, uint32_t* cout,
-           const int64_t* __restrict__ fstep, const double* __restrict__ fdose, double* __restrict__ cum_dose,
-           uint32_t* __restrict__ intents, uint32_t* __restrict__ icount, uint32_t* __restrict__ tile_ctr,
-           int n_tiles, int pass, Params P) {
-    using S = Tma2Shape<TX, TY, K>;
-    constexpr int BX = S::BX, NB = S::NB, XL = S::XL, PX = S::PX, NP = S::NP;
-    constexpr int kS = kTmaStages;
-    constexpr uint32_t kStageBytes = 4u * NB * sizeof(float);
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    float* stage = reinterpret_cast<float*>(base);  // stage s: O2 [NB], glucose [NB], H+ [NB], cell words [NB]
-    float2* lv = reinterpret_cast<float2*>(base + (size_t)kS * kStageBytes);  // [level-1][parity][field][NP]
-    __shared__ __align__(8) uint64_t full[kS];
-    __shared__ float s_dose, s_dq;
-    __shared__ int s_tile;
-
-    const int tid = threadIdx.x;
-    const bool act = tid < NP;
-    const int px = tid % PX, ry = tid / PX;
-    const int xr = 2 * px - XL;   // column a relative to the tile's x0
-    const int yr = ry - (K - 1);  // row relative to the tile's y0
-    // level-l region membership of the two lanes (level l covers the tile plus K - l on every side)
-    bool la[K + 1], lb[K + 1];
-#pragma unroll
-    for (int l = 1; l <= K; ++l) {
-        const bool rowin = act && yr >= -(K - l) && yr < TY + (K - l);
-        la[l] = rowin && xr >= -(K - l) && xr < TX + (K - l);
-        lb[l] = rowin && xr + 1 >= -(K - l) && xr + 1 < TX + (K - l);
-    }
-    const int sb = (yr + kTmaHaloY) * BX + (xr + kTmaHaloX);  // column a in a staged plane (even)
-    float2* const my_lv = lv + tid;  // + (((l - 1) * 2 + parity) * 3 + f) * NP
-    const uint32_t lane = threadIdx.x & 31u;
-    const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
-    const float lam[3] = {P.lam[0], P.lam[1], P.lam[2]};
-    bool timed_out = false;
-
-    if (tid == 0)
-        for (int s = 0; s < kS; ++s) mbar_init(&full[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    __syncthreads();
-
-    const int64_t step = *clock + k_off;
-    uint32_t* cnt = icount + (step & 1);
-    uint32_t loaded_planes = 0;
-    for (;;) {
-    const int ti = next_tile(tile_ctr, step, pass, &s_tile);
-    if (ti >= n_tiles) break;
-    const Tile tl = tiles[ti];
-    const Proto pr = protos[tl.p];
-    if (step >= pr.t_end) continue;
-    if (threadIdx.x == 0) {
-        double q = 0.0;
-        const double d = first ? dose_at(pr, fstep, fdose, step, P.frac_cap, &q) : 0.0;
-        s_dose = (float)d;
-        s_dq = (float)q;
-        if (d > 0.0 && tl.x0 == 0 && tl.y0 == 0 && tl.z0 == 0) cum_dose[tl.p] += d;
-    }
-    const int L = pr.L;
-    const int LL = L * L;
-    const int xa = tl.x0 + xr, y = tl.y0 + yr;
-    const bool yin = act && y >= 0 && y < L;
-    const bool ina = yin && xa >= 0 && xa < L, inb = yin && xa + 1 >= 0 && xa + 1 < L;
-    const bool yface = y == 0 || y == L - 1;
-    const bool fa = !ina || yface || xa == 0 || xa == L - 1;  // pinned lanes (faces, outside the lattice)
-    const bool fb = !inb || yface || xa + 1 == 0 || xa + 1 == L - 1;
-    const bool outa = la[K] && ina, outb = lb[K] && inb;
-    // element offset of column a (column b alone: one element before it, only the second element accessed)
-    const int col = (ina || inb) ? xa + L * y : 0;
-    const int z0 = tl.z0, z1 = tl.z1;
-    const int zl0 = max(0, z0 - K), zl1 = min(L - 1, z1 - 1 + K);
-    float* const d0 = oO + pr.site0 + col;
-    float* const d1 = oG + pr.site0 + col;
-    float* const d2 = oH + pr.site0 + col;
-    uint32_t* const dC = cout + pr.site0 + col;
-    const CUtensorMap* mf = maps + (size_t)pr.tmap * kTmaArrays;
-    const int zb = (int)(pr.site0 / LL);
-    const int bx0 = tl.x0 - kTmaHaloX, by0 = tl.y0 - kTmaHaloY;
-    const uint32_t g0 = loaded_planes;
-
-    auto issue = [&](int j) {
-        if (tid == 0 && j <= zl1) {
-            const uint32_t n = g0 + (uint32_t)(j - zl0);
-            uint64_t* bar = &full[n & (kS - 1)];
-            float* dst = stage + (size_t)(n & (kS - 1)) * 4 * NB;
-            mbar_expect_tx(bar, kStageBytes);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) tma_load_3d(dst + a * NB, mf + map_in + a, bx0, by0, zb + j, bar);
-            tma_load_3d(dst + 3 * NB, mf + map_cin, bx0, by0, zb + j, bar);
-        }
-    };
-
-    float2 ring[K][3][3];  // ring[l][f][(plane - zl0) mod 3]: level l of field f, lanes (a, b)
-#pragma unroll
-    for (int l = 0; l < K; ++l)
-#pragma unroll
-        for (int f = 0; f < 3; ++f)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) ring[l][f][j] = f2(0.f, 0.f);
-    uint2 wr[3] = {make_uint2(0, 0), make_uint2(0, 0), make_uint2(0, 0)};
-    uint32_t hit = 0;  // bit 2 * slot + lane: the word was changed by irradiation
-
-#pragma unroll
-    for (int j = 0; j < kDepth; ++j) issue(zl0 + j);
-    __syncthreads();
-    const float dose = s_dose;
-    const int n_it = zl1 + K - zl0 + 1;
-    const int i_lo = max(max(zl0 + 2 * K, z0 + K), K + 1);
-    const int i_hi = min(min(zl1, z1 - 1 + K), L - 2);
-    auto iteration = [&](auto phc, auto chkc, const int i) {
-        constexpr int ph = decltype(phc)::value;
-        constexpr bool CHK = decltype(chkc)::value;
-        __syncthreads();
-        issue(i + kDepth);
-        const bool loaded = !CHK || i <= zl1;
-        const uint32_t n = g0 + (uint32_t)(i - zl0);
-        const float* st = stage + (size_t)(n & (kS - 1)) * 4 * NB + sb;
-        if (loaded && !timed_out && !mbar_wait(&full[n & (kS - 1)], (n / kS) & 1u)) {
-            timed_out = true;
-            if (P.status) atomicOr(P.status, kStatusTmaTimeout);
-        }
-        float2 v0[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
-        uint2 w = make_uint2(0, 0);
-        if (loaded && act) {
-#pragma unroll
-            for (int f = 0; f < 3; ++f) v0[f] = *reinterpret_cast<const float2*>(st + f * NB);
-            w = *reinterpret_cast<const uint2*>(st + 3 * NB);
-        }
-        if (dose > 0.f && loaded && (!CHK || (i > 0 && i < L - 1))) {
-#pragma unroll
-            for (int ln = 0; ln < 2; ++ln) {
-                uint32_t& wl = ln ? w.y : w.x;
-                const bool fl = ln ? fb : fa;
-                const uint32_t kind = wl & kKindMask;
-                if (fl || kind == kEmpty) continue;
-                const float Sv = lq_survival(kind, ln ? v0[0].y : v0[0].x, dose, s_dq, P);
-                const int s = xa + ln + L * y + LL * i;
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)step, kPurposeIrr, (uint32_t)tl.p),
-                                              P.key0, P.key1);
-                if (u24(r.x) >= Sv) {
-                    const uint32_t nw = (P.flags & kFDoomImmediate) ? kEmpty : (wl | kDoomed);
-                    if (nw != wl) hit |= 1u << (2 * ph + ln);
-                    wl = nw;
-                }
-            }
-        }
-        wr[ph] = w;
-#pragma unroll
-        for (int f = 0; f < 3; ++f) ring[0][f][ph] = v0[f];
-#pragma unroll
-        for (int l = 1; l <= K; ++l) {
-            const int q = i - l;
-            const int sq = (ph - l + 6) % 3, sm = (ph - l - 1 + 6) % 3, sp = (ph - l + 1 + 6) % 3;
-            bool ra = la[l], rb = lb[l];
-            if constexpr (CHK) {
-                const int lo = (zl0 == 0) ? 0 : zl0 + l;
-                const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
-                const bool zin = q >= lo && q <= hi;
-                ra = ra && zin;
-                rb = rb && zin;
-            }
-            float2 v[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
-            if (ra || rb) {
-                const bool zface = CHK && (q == 0 || q == L - 1);
-                const bool pa = fa || zface, pb = fb || zface;  // pinned (Dirichlet) lanes
-#pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    const float2 c = ring[l - 1][f][sq];
-                    float2 t = c;
-                    if (diffuse && !(pa && pb)) {
-                        float2 up, dn;
-                        float left, right;
-                        if (l == 1) {  // level-0 neighbours from the staged plane q
-                            const float* pf =
-                                stage + (size_t)((g0 + (uint32_t)(q - zl0)) & (kS - 1)) * 4 * NB + f * NB + sb;
-                            up = *reinterpret_cast<const float2*>(pf - BX);
-                            dn = *reinterpret_cast<const float2*>(pf + BX);
-                            left = pf[-1];
-                            right = pf[2];
-                        } else {  // level l-1 neighbours from its shared plane (pairs of the neighbouring threads)
-                            const float2* pv = my_lv + ((((l >= 2 ? l - 2 : 0) * 2 + (q & 1)) * 3) + f) * NP;
-                            up = pv[-PX];
-                            dn = pv[PX];
-                            left = pv[-1].y;
-                            right = pv[1].x;
-                        }
-                        t = stencil_t2(c, f2(left, c.x), f2(c.y, right), up, dn, ring[l - 1][f][sm],
-                                       ring[l - 1][f][sp], lam[f]);
-                    }
-                    v[f] = t;
-                }
-                float2 uO = f2(0.f, 0.f), uG = f2(0.f, 0.f), pHv = f2(0.f, 0.f);
-                const uint32_t ka = pa ? kEmpty : (wr[sq].x & kKindMask), kb = pb ? kEmpty : (wr[sq].y & kKindMask);
-                if (react && (ka != kEmpty || kb != kEmpty))
-                    uptake2(ka, kb, ring[l - 1][0][sq], ring[l - 1][1][sq], P, uO, uG, pHv);
-                const float2 o0 = __fadd2_rn(v[0], f2(-uO.x, -uO.y));
-                const float2 o1 = __fadd2_rn(v[1], f2(-uG.x, -uG.y));
-                const float2 o2 = __fadd2_rn(v[2], pHv);
-                const float2 c0 = ring[l - 1][0][sq], c1 = ring[l - 1][1][sq], c2 = ring[l - 1][2][sq];
-                v[0] = f2(pa ? c0.x : fmaxf(o0.x, 0.f), pb ? c0.y : fmaxf(o0.y, 0.f));
-                v[1] = f2(pa ? c1.x : fmaxf(o1.x, 0.f), pb ? c1.y : fmaxf(o1.y, 0.f));
-                v[2] = f2(pa ? c2.x : fmaxf(o2.x, 0.f), pb ? c2.y : fmaxf(o2.y, 0.f));
-            }
-            if (l < K) {
-#pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    ring[l][f][sq] = v[f];
-                    if (act) my_lv[(((l - 1) * 2 + (q & 1)) * 3 + f) * NP] = v[f];
-                }
-            } else {
-                const bool oz = !CHK || (q >= z0 && q < z1);
-                const bool oa = outa && oz, ob = outb && oz;
-                bool wa = false, wb = false;
-                const int o = q * LL;
-                if ((oa || ob) && (!oa || site_ok(P, pr.site0 + col + o)) &&
-                    (!ob || site_ok(P, pr.site0 + col + o + 1))) {
-                    const bool zface = CHK && (q == 0 || q == L - 1);
-                    const bool sa = oa && !fa && !zface, sb2 = ob && !fb && !zface;  // interior sites written
-                    if (sa && sb2) {
-                        *reinterpret_cast<float2*>(d0 + o) = v[0];
-                        *reinterpret_cast<float2*>(d1 + o) = v[1];
-                        *reinterpret_cast<float2*>(d2 + o) = v[2];
-                    } else {
-                        if (sa) {
-                            d0[o] = v[0].x;
-                            d1[o] = v[1].x;
-                            d2[o] = v[2].x;
-                        }
-                        if (sb2) {
-                            d0[o + 1] = v[0].y;
-                            d1[o + 1] = v[1].y;
-                            d2[o + 1] = v[2].y;
-                        }
-                    }
-                    const uint2 w0 = wr[sq];
-                    if (EPI) {
-                        const uint32_t na = sa ? update_cell(w0.x, v[0].x, v[1].x, v[2].x, P, wa) : w0.x;
-                        const uint32_t nb = sb2 ? update_cell(w0.y, v[0].y, v[1].y, v[2].y, P, wb) : w0.y;
-                        if (oa && ob) *reinterpret_cast<uint2*>(dC + o) = make_uint2(na, nb);
-                        else {
-                            if (oa) dC[o] = na;
-                            if (ob) dC[o + 1] = nb;
-                        }
-                    } else {
-                        if (oa && (hit >> (2 * sq) & 1u)) dC[o] = w0.x;
-                        if (ob && (hit >> (2 * sq + 1) & 1u)) dC[o + 1] = w0.y;
-                    }
-                }
-                hit &= ~(3u << (2 * sq));  // the slot is reused by plane q + 3
-                if (EPI) {
-                    const uint32_t ma = __ballot_sync(0xffffffffu, wa), mb = __ballot_sync(0xffffffffu, wb);
-                    if (ma | mb) {
-                        const uint32_t leader = __ffs(ma | mb) - 1;
-                        uint32_t slot = 0;
-                        if (lane == leader) slot = atomicAdd(cnt, (uint32_t)(__popc(ma) + __popc(mb)));
-                        slot = __shfl_sync(0xffffffffu, slot, leader);
-                        const uint32_t lt = (1u << lane) - 1u;
-                        const uint32_t g = (uint32_t)(pr.site0 + col + o);
-                        const uint32_t ata = slot + __popc(ma & lt), atb = slot + __popc(ma) + __popc(mb & lt);
-                        if (wa && site_ok(P, ata)) intents[ata] = g;
-                        if (wb && site_ok(P, atb)) intents[atb] = g + 1;
-                    }
-                }
-            }
-        }
-    };
-    using I0 = std::integral_constant<int, 0>;
-    using I1 = std::integral_constant<int, 1>;
-    using I2 = std::integral_constant<int, 2>;
-    using Checked = std::integral_constant<bool, true>;
-    using Unchecked = std::integral_constant<bool, false>;
-    int ib = 0;
-    for (; ib < n_it && zl0 + ib < i_lo; ib += 3) {
-        iteration(I0{}, Checked{}, zl0 + ib);
-        if (ib + 1 < n_it) iteration(I1{}, Checked{}, zl0 + ib + 1);
-        if (ib + 2 < n_it) iteration(I2{}, Checked{}, zl0 + ib + 2);
-    }
-    for (; ib + 2 < n_it && zl0 + ib + 2 <= i_hi; ib += 3) {
-        iteration(I0{}, Unchecked{}, zl0 + ib);
-        iteration(I1{}, Unchecked{}, zl0 + ib + 1);
-        iteration(I2{}, Unchecked{}, zl0 + ib + 2);
-    }
-    for (; ib < n_it; ib += 3) {
-        iteration(I0{}, Checked{}, zl0 + ib);
-        if (ib + 1 < n_it) iteration(I1{}, Checked{}, zl0 + ib + 1);
-        if (ib + 2 < n_it) iteration(I2{}, Checked{}, zl0 + ib + 2);
-    }
-    loaded_planes = g0 + (uint32_t)(zl1 - zl0 + 1);
-    }
-    if (timed_out && tid == 0)
-        for (uint32_t n = (loaded_planes > kS ? loaded_planes - kS : 0); n < loaded_planes; ++n)
-            (void)mbar_wait(&full[n & (kS - 1)], (n / kS) & 1u);
-}
-
 }  // namespace simdev
