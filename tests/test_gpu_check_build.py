@@ -19,7 +19,8 @@ def cuda():
     return torch
 
 
-@pytest.mark.parametrize("path,shape", [("fused", 3), ("fused", 4), ("fused", 1), ("substep", 0)])
+@pytest.mark.parametrize("path,shape", [("fused", 3), ("fused", 4), ("fused", 1), ("fused", 5), ("fused", 6),
+                                        ("substep", 0)])
 def test_checked_build_stays_in_bounds_and_matches(cuda, path, shape):
     from paper_2303_08123_b300 import Simulator, csr
     from synth import workloads
