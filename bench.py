@@ -313,7 +313,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     sim = Simulator(Ls, Rs, seed=SEED, precision=args.precision, hours=hours, params=PARAMS,
-                    dose_cap_gy=30.0, device=dev, path=args.path, tile_shape=args.tile_shape,
+                    dose_cap_gy=30.0, device=dev, path=args.path, tile_shape=args.tile_shape, z_chunk=args.z_chunk,
                     t_end_steps=t_end_steps())
     sim.load_protocols(off, d, w)
     if args.path == "fused" and args.tile_shape == 0:
@@ -490,7 +490,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "substep"])
-    ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-4 (0: autotune)")
+    ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-6 (0: autotune)")
+    ap.add_argument("--z-chunk", type=int, default=0, help="planes per fused CTA (0: split to fill the GPU)")
     ap.add_argument("--workload", default="ragged", choices=["ga_batch", "ragged", "single"],
                     help="ragged: 1,024 protocols on 32^3-112^3 (default); ga_batch: 256 x 64^3; "
                          "single: one protocol on 40^3 for 288 h")

@@ -261,11 +261,14 @@ sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, doubl
 
 /*
  * Autotuner of the fused path: time n_steps plain steps of this context's own
- * batch with every applicable tile shape (sim_config.tile_shape 1..6), keep the
- * fastest, then re-seed every spheroid and set the clock to 0 (call it right
- * after sim_load_protocols).  *best (may be NULL) receives the chosen shape
- * (0 on the substep path); ms (6 entries, may be NULL) the device milliseconds
- * per step of each shape, -1 where a shape does not apply.  Synchronises.
+ * batch with every applicable tile shape (sim_config.tile_shape 1..6) -- on a
+ * batch with too few column tiles to fill the GPU (split in z unless
+ * sim_config.z_chunk fixes the split) each shape also with a finer z split of
+ * 2 planes per CTA -- keep the fastest, then re-seed every spheroid and set the
+ * clock to 0 (call it right after sim_load_protocols).  *best (may be NULL)
+ * receives the chosen shape (0 on the substep path); ms (6 entries, may be
+ * NULL) the device milliseconds per step of each shape (its faster split), -1
+ * where a shape does not apply.  Synchronises.
  */
 sim_status sim_autotune(sim_ctx* ctx, int n_steps, int* best, double* ms);
 

@@ -150,10 +150,13 @@ int pick_shape(const sim_config& cfg, int n, const int32_t* L) {
     return tiles[3] >= kTargetCtas ? 3 : 4;
 }
 
+constexpr int kFineZ = 2;  // the finer z split the autotuner also tries on batches with too few columns
+
 // Fused work list: column tiles of every protocol still running (live[p] != 0;
-// live == nullptr: all), split in z when those have too few columns to fill the GPU.
+// live == nullptr: all), split in z when those have too few columns to fill the
+// GPU (chunks of at least 8 planes, or of fine_z planes when fine_z > 0).
 std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int shape,
-                             const uint8_t* live = nullptr) {
+                             const uint8_t* live = nullptr, int fine_z = 0) {
     const int TX = kTileShapes[shape][0], TY = kTileShapes[shape][1];
     int64_t cols = 0;
     for (int p = 0; p < n; ++p)
@@ -166,7 +169,8 @@ std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int
         else if (cols < kTargetCtas) {
             const int64_t nz = (kTargetCtas + cols - 1) / cols;
             zc = (int)((L[p] + nz - 1) / nz);
-            if (zc < 8) zc = 8;
+            if (fine_z > 0) zc = fine_z;
+            else if (zc < 8) zc = 8;
         }
         for (int z = 0; z < L[p]; z += zc)
             for (int y = 0; y < L[p]; y += TY)
@@ -185,6 +189,15 @@ std::vector<Tile> make_tiles(const sim_config& cfg, int n, const int32_t* L, int
     return t;
 }
 
+// True if the batch has too few columns to fill the GPU, so that its work list is split in z.
+bool z_split_applies(const sim_config& cfg, int n, const int32_t* L, int shape) {
+    if (cfg.z_chunk > 0) return false;
+    const int TX = kTileShapes[shape][0], TY = kTileShapes[shape][1];
+    int64_t cols = 0;
+    for (int p = 0; p < n; ++p) cols += (int64_t)((L[p] + TX - 1) / TX) * ((L[p] + TY - 1) / TY);
+    return cols < kTargetCtas;
+}
+
 }  // namespace
 
 struct sim_ctx {
@@ -196,6 +209,7 @@ struct sim_ctx {
     std::vector<Tile> tiles;
     std::vector<uint8_t> tile_live;  // protocols the fused work list covers
     int shape = 1;
+    int fine_z = 0;  // > 0: the autotuner chose the finer z split (chunks of this many planes)
     int vec_ok = 1;  // every lattice side even: column pairs start on even elements
     int64_t total_sites = 0;
     Layout lay{};
@@ -712,7 +726,7 @@ void launch_totals(sim_ctx* c) {
 // Switch the fused work list to tile shape `sh` (rebuilds and uploads the tiles; drops captured graphs).
 sim_status set_shape(sim_ctx* c, int sh, const std::vector<int32_t>& L) {
     c->shape = sh;
-    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh, c->tile_live.data());
+    c->tiles = make_tiles(c->cfg, c->n, L.data(), sh, c->tile_live.data(), c->fine_z);
     drop_graphs(c);
     cudaError_t e = cudaMemcpyAsync(c->ws + c->lay.tiles, c->tiles.data(), sizeof(Tile) * c->tiles.size(),
                                     cudaMemcpyHostToDevice, c->stream);
@@ -767,11 +781,12 @@ sim_status sim_workspace_size(const sim_config* cfg, int n, const int32_t* L, si
     }
     const int64_t total = place_protocols(n, L, nullptr);
     if (total >= (int64_t)0xffffffffLL) return SIM_EINVAL;  // work list holds 32-bit site indices
-    int64_t nt = 0;  // room for the work list of any shape the autotuner may pick
-    for (int sh = 1; sh <= kNumShapes; ++sh) {
-        const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
-        nt = t > nt ? t : nt;
-    }
+    int64_t nt = 0;  // room for the work list of any shape and z split the autotuner may pick
+    for (int sh = 1; sh <= kNumShapes; ++sh)
+        for (int fz : {0, kFineZ}) {
+            const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh, nullptr, fz).size();
+            nt = t > nt ? t : nt;
+        }
     *bytes = make_layout(*cfg, n, total, nb, nt, side_classes(n, L)).total;
     return SIM_OK;
 }
@@ -837,10 +852,11 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
     c->tiles = make_tiles(*cfg, n, L, c->shape);
     c->tile_live.assign(n, 1);
     int64_t nt = 0;
-    for (int sh = 1; sh <= kNumShapes; ++sh) {
-        const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh).size();
-        nt = t > nt ? t : nt;
-    }
+    for (int sh = 1; sh <= kNumShapes; ++sh)
+        for (int fz : {0, kFineZ}) {
+            const int64_t t = (int64_t)make_tiles(*cfg, n, L, sh, nullptr, fz).size();
+            nt = t > nt ? t : nt;
+        }
     c->lay = make_layout(*cfg, n, site0, (int64_t)c->blocks.size(), nt, c->n_sides);
     c->P.n_sites = (uint64_t)site0;
     c->P.status = c->at<uint32_t>(c->lay.status);
@@ -1077,33 +1093,39 @@ sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) || cudaEventCreate(&b)) return fail(c, SIM_ECUDA, "event create");
     double best_ms = -1.0;
-    int pick = c->shape;
+    int pick = c->shape, pick_z = 0;
     sim_status st = SIM_OK;
-    for (int sh = 1; sh <= kNumShapes && st == SIM_OK; ++sh) {
-        if (tma_shape(sh) && !c->tma_ok) continue;
-        st = set_shape(c, sh, L);
-        // one untimed step (first touch), then n_steps timed plain steps
-        for (int i = 0; i <= n_steps && st == SIM_OK; ++i) {
-            if (i == 1) cudaEventRecord(a, c->stream);
-            st = step_dispatch(c, c->stream, 0, c->cur, c->ccur);
-            if (!st) st = tick(c, c->stream, 1);
-            advance(c, 1);
+    // every applicable shape; on a batch split in z to fill the GPU, each shape also with the finer split
+    // (shorter z ranges per CTA: more halo work, less latency per pass)
+    for (int sh = 1; sh <= kNumShapes && st == SIM_OK; ++sh)
+        for (int fz : {0, kFineZ}) {
+            if (tma_shape(sh) && !c->tma_ok) continue;
+            if (fz && !z_split_applies(c->cfg, c->n, L.data(), sh)) continue;
+            c->fine_z = fz;
+            st = set_shape(c, sh, L);
+            // one untimed step (first touch), then n_steps timed plain steps
+            for (int i = 0; i <= n_steps && st == SIM_OK; ++i) {
+                if (i == 1) cudaEventRecord(a, c->stream);
+                st = step_dispatch(c, c->stream, 0, c->cur, c->ccur);
+                if (!st) st = tick(c, c->stream, 1);
+                advance(c, 1);
+            }
+            if (st) break;
+            cudaEventRecord(b, c->stream);
+            cudaError_t e = cudaEventSynchronize(b);
+            if (e) {
+                st = cuda_check(c, e, "autotune sync");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, a, b);
+            if (ms && (ms[sh - 1] < 0 || t / n_steps < ms[sh - 1])) ms[sh - 1] = t / n_steps;
+            if (best_ms < 0 || t < best_ms) best_ms = t, pick = sh, pick_z = fz;
         }
-        if (st) break;
-        cudaEventRecord(b, c->stream);
-        cudaError_t e = cudaEventSynchronize(b);
-        if (e) {
-            st = cuda_check(c, e, "autotune sync");
-            break;
-        }
-        float t = 0.f;
-        cudaEventElapsedTime(&t, a, b);
-        if (ms) ms[sh - 1] = t / n_steps;
-        if (best_ms < 0 || t < best_ms) best_ms = t, pick = sh;
-    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st) return st;
+    c->fine_z = pick_z;
     st = set_shape(c, pick, L);
     if (best) *best = pick;
     if (!st) st = reset_device(c);  // the timing steps advanced the batch: start it again from step 0
