@@ -647,3 +647,25 @@ def test_near_band_of_the_irradiation_draw(orc, k, flagged):
     assert bool(flags & 1) == flagged and flags & ~1 == 0, (k, flags)
     assert stats["n_near"] == int(flagged) and stats["n_decisions"] == 1
     assert stats["n_doomed_new"] == int(u >= S_target)
+
+
+# ----------------------------------------------------------------------------- stored oracle results
+def test_single_protocol_golden_was_written_by_this_oracle(orc):
+    """tests/golden/single_protocol_288h.json (the oracle's whole 288 h run the
+    GPU test compares with) is consistent with the oracle as it stands: its
+    first two hourly counts equal a fresh oracle run of 1,200 steps, its 289
+    counts start at the 515 cells of the R = 5 ball, and its central plane and
+    decision statistics have the stated shape."""
+    import json
+    import os
+    from synth import workloads
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "single_protocol_288h.json")) as f:
+        g = json.load(f)
+    doses, waits = workloads.daily_fractions(10, 2.0, 24.0)
+    assert g["doses"] == doses and g["waits"] == waits and g["L"] == 40 and g["R"] == 5
+    assert len(g["counts"]) == 289 and g["counts"][0] == 515
+    ref = orc.run(P0, 40, 5, g["seed"], 0, doses, waits, t_end_steps=1200, hours=2)
+    assert ref["counts"].tolist() == g["counts"][:3]
+    assert len(g["central_plane"]["O"]) == 40 * 40 and len(g["final_cells_sha256"]) == 64
+    assert g["stats"]["n_near"] == 0 and g["stats"]["n_decisions"] > 10 ** 8
+    assert sum(g["final_kind_histogram"]) == 40 ** 3 and g["cum_dose"] == 20.0
