@@ -237,7 +237,8 @@ int gemm(const void* A, const void* B, float* C, int M, int N, int K, uint32_t* 
             return -3;
         attr = true;
     }
-    tcg::k_gemm_bf16<<<M / tcg::kRows, tcg::kThreads, tcg::kSmemBytes, s>>>(
+    const dim3 grid((unsigned)(M / tcg::kRows), (unsigned)((N + tcg::kCols - 1) / tcg::kCols));
+    tcg::k_gemm_bf16<<<grid, tcg::kThreads, tcg::kSmemBytes, s>>>(
         (const __nv_bfloat16*)A, (const __nv_bfloat16*)B, C, M, N, K, status);
     return cuda_status(cudaGetLastError());
 }

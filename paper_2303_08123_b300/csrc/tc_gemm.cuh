@@ -3,14 +3,16 @@
 //
 //   C[M x N] (FP32, row-major) = A[M x K] * B[N x K]^T   (A, B BF16, K contiguous)
 //
-// One CTA (4 warps) owns a 128-row tile of C and all N <= 256 columns.  The
-// accumulator lives in tensor memory (TMEM): lane = row, column = output column.
-// K advances in chunks of 64: all threads stage the chunk of A and B in shared
-// memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
-// core matrix), one elected thread issues the tcgen05.mma instructions
-// (M = 128, N, K = 16 each) and tcgen05.commit makes an mbarrier arrive when
-// they have finished reading shared memory.  The epilogue reads TMEM with
-// tcgen05.ld (each warp its 32 lanes) and stores FP32 rows.
+// One CTA (4 warps) owns a 128-row x (up to) 64-column tile of C, so that a
+// 4,096 x 256 product runs on 128 CTAs.  The accumulator lives in tensor memory
+// (TMEM): lane = row, column = output column.  K advances in chunks of 64,
+// double-buffered: all threads stage chunk c + 1 of A and B in shared memory (in
+// the no-swizzle K-major core-matrix layout, 8 rows x 16 bytes per core matrix)
+// while the tensor cores work on chunk c; one elected thread issues the
+// tcgen05.mma instructions (M = 128, N, K = 16 each), and tcgen05.commit makes
+// the buffer's mbarrier arrive when they have finished reading it.  A buffer is
+// restaged only after that arrival.  The epilogue reads TMEM with tcgen05.ld
+// (each warp its 32 lanes) and stores FP32 rows.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -24,14 +26,17 @@ constexpr int kCoreBytes = 128;               // 8 rows x 16 bytes
 constexpr int kSbo = (kChunk / 8) * kCoreBytes;  // bytes between 8-row groups (1024)
 constexpr uint32_t kSpinLimit = 1u << 26;     // bounded mbarrier wait
 
-// bytes of the staged A (128 x 64) and B (<= 256 x 64) chunks, padded so that
-// any reading of the descriptor's two byte offsets stays inside the buffer
+constexpr int kCols = 64;      // N per CTA (columns of C)
+// bytes of one staged A (128 x 64) and B (<= 64 x 64) chunk
 constexpr int kABytes = (kRows / 8) * kSbo;
-constexpr int kBBytes = (256 / 8) * kSbo;
-// requested dynamic shared memory: at most two CTAs fit on one SM, so their
-// 2 x 256 TMEM columns never exceed the SM's 512 and tcgen05.alloc never waits
-constexpr int kSmemBytes = 100 * 1024;
-static_assert(kABytes + kBBytes + 64 <= kSmemBytes, "staging buffers exceed the shared-memory request");
+constexpr int kBBytes = (kCols / 8) * kSbo;
+constexpr int kBufBytes = kABytes + kBBytes;
+// requested dynamic shared memory: two buffers and the barriers; at most four
+// CTAs fit on one SM, so their 4 x 64 TMEM columns never exceed the SM's 512 and
+// tcgen05.alloc never waits
+constexpr int kSmemBytes = 52 * 1024;
+static_assert(2 * kBufBytes + 64 <= kSmemBytes, "staging buffers exceed the shared-memory request");
+static_assert(5 * kSmemBytes > 228 * 1024, "more than four CTAs per SM could exhaust the tensor memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -127,22 +132,25 @@ __device__ __forceinline__ void stage(unsigned char* dst, const __nv_bfloat16* _
     }
 }
 
-// C = A * B^T for one 128-row tile (blockIdx.x); N in {16, 32, ..., 256}, K a
-// multiple of 16, M a multiple of 128.  *status != 0 after a timed-out wait.
+// C = A * B^T for one tile: rows 128 blockIdx.x.., columns 64 blockIdx.y..; N a
+// multiple of 16 (<= 256), K a multiple of 16, M a multiple of 128.  *status != 0
+// after a timed-out wait.
 __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __restrict__ A,
                                                         const __nv_bfloat16* __restrict__ B, float* __restrict__ C,
                                                         int M, int N, int K, uint32_t* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + kABytes;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kABytes + kBBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kABytes + kBBytes + 8);
+    // buffer b: A chunk at smem + b * kBufBytes, B chunk kABytes after it
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);  // one per buffer
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * kBufBytes + 16);
     __shared__ int s_fail;
     const int warp = threadIdx.x / 32;
-    const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+    const int n0 = blockIdx.y * kCols;
+    const int nt = (N - n0) < kCols ? (N - n0) : kCols;  // columns of this tile (a multiple of 16)
+    const uint32_t ncols = nt <= 32 ? 32u : 64u;
     if (warp == 0) tmem_alloc(tslot, ncols);
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -151,12 +159,24 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __r
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const int m0 = blockIdx.x * kRows;
-    const uint32_t idesc = instr_desc(kRows, N);
-    uint32_t phase = 0;
-    for (int k0 = 0; k0 < K; k0 += kChunk) {
+    const uint32_t idesc = instr_desc(kRows, nt);
+    const int n_chunks = (K + kChunk - 1) / kChunk;
+    uint32_t phase0 = 0u, phase1 = 0u;  // parity of the next completion of each buffer's barrier
+    int committed = 0;  // chunks whose MMAs were issued
+    for (int c = 0; c < n_chunks; ++c) {
+        const int buf = c & 1;
+        if (c >= 2) {  // the MMAs of chunk c - 2 must be done reading this buffer
+            if (threadIdx.x == 0 && !mbar_wait(&bar[buf], buf ? phase1 : phase0)) s_fail = 1;
+            (buf ? phase1 : phase0) ^= 1u;
+            __syncthreads();
+            if (s_fail) break;
+        }
+        const int k0 = c * kChunk;
         const int kc = (K - k0) < kChunk ? (K - k0) : kChunk;
+        unsigned char* sA = smem + buf * kBufBytes;
+        unsigned char* sB = sA + kABytes;
         stage(sA, A + (size_t)m0 * K, kRows, K, k0, kc);
-        stage(sB, B, N, K, k0, kc);
+        stage(sB, B + (size_t)n0 * K, nt, K, k0, kc);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy stores -> async proxy
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -164,25 +184,32 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __r
             for (int ks = 0; ks < kc / 16; ++ks) {
                 const uint64_t da = smem_desc(smem_u32(sA) + ks * 2 * kCoreBytes, kCoreBytes, kSbo);
                 const uint64_t db = smem_desc(smem_u32(sB) + ks * 2 * kCoreBytes, kCoreBytes, kSbo);
-                mma_bf16(tmem, da, db, idesc, (k0 > 0 || ks > 0) ? 1u : 0u);
+                mma_bf16(tmem, da, db, idesc, (c > 0 || ks > 0) ? 1u : 0u);
             }
-            mma_commit(bar);
-            if (!mbar_wait(bar, phase)) s_fail = 1;  // staged chunk consumed (or timed out)
+            mma_commit(&bar[buf]);
         }
-        phase ^= 1u;
-        __syncthreads();
-        if (s_fail) break;
+        committed = c + 1;
     }
+    // the last (up to two) commits: every MMA has finished and the accumulator is complete
+    if (threadIdx.x == 0)
+        for (int c = committed >= 2 ? committed - 2 : 0; c < committed; ++c) {
+            const int buf = c & 1;
+            if (!mbar_wait(&bar[buf], buf ? phase1 : phase0)) s_fail = 1;
+            (buf ? phase1 : phase0) ^= 1u;
+        }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {
         const int row = m0 + warp * 32 + (threadIdx.x & 31);
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int cb = 0; cb < N; cb += 32) {
+        for (int cb = 0; cb < nt; cb += 32) {
             float v[32];
             tmem_ld32(tmem + lane_base + (uint32_t)cb, v);
-            const int nv = (N - cb) < 32 ? (N - cb) : 32;
-            float* dst = C + (size_t)row * N + cb;
-            for (int j = 0; j < nv; ++j) dst[j] = v[j];
+            const int nv = (nt - cb) < 32 ? (nt - cb) : 32;
+            float* dst = C + (size_t)row * N + n0 + cb;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < nv) dst[j] = v[j];
         }
     } else if (threadIdx.x == 0) {
         atomicExch(status, 1u);

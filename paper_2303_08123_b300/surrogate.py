@@ -173,6 +173,26 @@ def main():
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / n
         out[name] = {"ms": ms, "gemm_tflops": flop / (ms / 1e3) / 1e12}
+    # one GEMM at the network's widths over many rows: what the tensor-core kernel sustains when it has work
+    lib = load_library()
+    M, N, K = 65536, 256, 256
+    A = torch.randn(M, K, device=net.device).to(torch.bfloat16)
+    Bm = torch.randn(N, K, device=net.device).to(torch.bfloat16)
+    C = torch.empty(M, N, dtype=torch.float32, device=net.device)
+    st = torch.zeros(1, dtype=torch.int32, device=net.device)
+    call = lambda: lib.mlp_gemm_bf16(A.data_ptr(), Bm.data_ptr(), C.data_ptr(), M, N, K, st.data_ptr(),  # noqa: E731
+                                     net.stream.cuda_stream)
+    for _ in range(5):
+        _check(call())
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(net.stream)
+    for _ in range(n):
+        call()
+    b.record(net.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / n
+    out["gemm_65536x256x256"] = {"ms": ms, "tflops": 2.0 * M * N * K / (ms / 1e3) / 1e12,
+                                 "status": int(st.item())}
     print(json.dumps(out))
 
 

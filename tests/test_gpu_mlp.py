@@ -17,7 +17,8 @@ def cuda():
     return torch
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 16, 16), (128, 48, 48), (256, 256, 96), (384, 112, 512), (128, 256, 256)])
+@pytest.mark.parametrize("M,N,K", [(128, 16, 16), (128, 48, 48), (256, 256, 96), (384, 112, 512), (128, 256, 256),
+                                   (256, 256, 4096), (128, 80, 208)])
 def test_tcgen05_gemm_matches_exact_product(cuda, M, N, K):
     torch = cuda
     from paper_2303_08123_b300.surrogate import gemm_bf16
