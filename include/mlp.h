@@ -60,8 +60,9 @@ int mlp_get_params(mlp_ctx* ctx, float* host);
 int mlp_set_params(mlp_ctx* ctx, const float* host);
 
 /* C[M x N] (device FP32) = A[M x K] * B[N x K]^T (device BF16, row-major)
- * on the tensor cores; M a multiple of 128, N a multiple of 16 up to 256, K a
- * multiple of 16.  d_status (device u32) is set non-zero if a bounded wait
+ * on the tensor cores, operands staged by TMA; M a multiple of 128, N a
+ * multiple of 16 up to 256, K a multiple of 16, d_A, d_B and d_C 16-byte
+ * aligned (-1 otherwise).  d_status (device u32) is set non-zero if a bounded wait
  * timed out.  Asynchronous. */
 int mlp_gemm_bf16(const void* d_A, const void* d_B, float* d_C, int M, int N, int K, uint32_t* d_status,
                   void* cuda_stream);

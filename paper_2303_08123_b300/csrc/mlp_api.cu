@@ -229,17 +229,67 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? 0 : -3; }
 
+// Tensor map of a row-major BF16 matrix [rows x K] for the GEMM's staging: x = K
+// column, y = row, a box of 8 K-columns by box_rows rows (rows beyond the matrix
+// read as zeros).  The driver's encoder is reached through the runtime.
+bool encode_operand(CUtensorMap* m, const void* base, int rows, int K, int box_rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor map of the FP32 result C [M x N] for the epilogue's stores: boxes of 32
+// columns (128 bytes) by 128 rows in the 128-byte swizzle; columns beyond N are
+// not written.
+bool encode_result(CUtensorMap* m, float* base, int M, int N) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+    const cuuint64_t strides[1] = {(cuuint64_t)N * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)tcg::kRows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int gemm(const void* A, const void* B, float* C, int M, int N, int K, uint32_t* status, cudaStream_t s) {
     if (M <= 0 || M % tcg::kRows || N < 16 || N > 256 || N % 16 || K <= 0 || K % 16) return -1;
+    if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || (uintptr_t)C % 16) return -1;  // tensor-map bases: 16-byte aligned
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(tcg::k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::kSmemBytes))
             return -3;
         attr = true;
     }
+    CUtensorMap mapA, mapB, mapC;
+    if (!encode_operand(&mapA, A, M, K, tcg::kRows) || !encode_operand(&mapB, B, N, K, tcg::kCols) ||
+        !encode_result(&mapC, C, M, N))
+        return -3;
     const dim3 grid((unsigned)(M / tcg::kRows), (unsigned)((N + tcg::kCols - 1) / tcg::kCols));
-    tcg::k_gemm_bf16<<<grid, tcg::kThreads, tcg::kSmemBytes, s>>>(
-        (const __nv_bfloat16*)A, (const __nv_bfloat16*)B, C, M, N, K, status);
+    tcg::k_gemm_bf16<<<grid, tcg::kThreads, tcg::kSmemBytes, s>>>(mapA, mapB, mapC, M, N, K, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -6,15 +6,20 @@
 // One CTA (4 warps) owns a 128-row x (up to) 64-column tile of C, so that a
 // 4,096 x 256 product runs on 128 CTAs.  The accumulator lives in tensor memory
 // (TMEM): lane = row, column = output column.  K advances in chunks of 64,
-// double-buffered: all threads stage chunk c + 1 of A and B in shared memory (in
-// the no-swizzle K-major core-matrix layout, 8 rows x 16 bytes per core matrix)
-// while the tensor cores work on chunk c; one elected thread issues the
-// tcgen05.mma instructions (M = 128, N, K = 16 each), and tcgen05.commit makes
-// the buffer's mbarrier arrive when they have finished reading it.  A buffer is
-// restaged only after that arrival.  The epilogue reads TMEM with tcgen05.ld
-// (each warp its 32 lanes) and stores FP32 rows.
+// double-buffered and staged by the tensor memory accelerator: per chunk one
+// thread issues one 2-D tiled bulk-tensor load per 8 K-columns of A (a 8 x 128
+// box) and of B (a 8 x 64 box).  A box lands as rows of 16 bytes, which is the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// 128 bytes between 8-row groups, one box between K groups).  The same thread
+// issues the tcgen05.mma instructions (M = 128, N, K = 16 each) once the
+// chunk's mbarrier reports its bytes, and tcgen05.commit makes a second
+// mbarrier arrive when they have finished reading the buffer, which is then
+// restaged with chunk c + 2 while chunk c + 1 is multiplied.  The epilogue reads
+// TMEM with tcgen05.ld (each warp its 32 lanes) into shared memory and writes the
+// FP32 tile with TMA stores.
 #pragma once
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 namespace tcg {
@@ -22,20 +27,20 @@ namespace tcg {
 constexpr int kRows = 128;     // M per CTA
 constexpr int kChunk = 64;     // K per staged chunk
 constexpr int kThreads = 128;  // 4 warps: one per 32 TMEM lanes
-constexpr int kCoreBytes = 128;               // 8 rows x 16 bytes
-constexpr int kSbo = (kChunk / 8) * kCoreBytes;  // bytes between 8-row groups (1024)
+constexpr int kCoreBytes = 128;  // 8 rows x 16 bytes: a core matrix, and the distance between 8-row groups
 constexpr uint32_t kSpinLimit = 1u << 26;     // bounded mbarrier wait
 
 constexpr int kCols = 64;      // N per CTA (columns of C)
-// bytes of one staged A (128 x 64) and B (<= 64 x 64) chunk
-constexpr int kABytes = (kRows / 8) * kSbo;
-constexpr int kBBytes = (kCols / 8) * kSbo;
+// bytes of one staged A (128 x 64) and B (64 x 64) chunk; one box of 8 K-columns is kRows (kCols) rows of 16 B
+constexpr int kABox = kRows * 16, kBBox = kCols * 16;
+constexpr int kABytes = (kChunk / 8) * kABox;
+constexpr int kBBytes = (kChunk / 8) * kBBox;
 constexpr int kBufBytes = kABytes + kBBytes;
 // requested dynamic shared memory: two buffers and the barriers; at most four
 // CTAs fit on one SM, so their 4 x 64 TMEM columns never exceed the SM's 512 and
 // tcgen05.alloc never waits
 constexpr int kSmemBytes = 52 * 1024;
-static_assert(2 * kBufBytes + 64 <= kSmemBytes, "staging buffers exceed the shared-memory request");
+static_assert(2 * kBufBytes + 1024 + 64 <= kSmemBytes, "staging buffers exceed the shared-memory request");
 static_assert(5 * kSmemBytes > 228 * 1024, "more than four CTAs per SM could exhaust the tensor memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -119,29 +124,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stage rows [0, rows) x K-columns [k0, k0 + kc) of a row-major BF16 matrix
-// (leading dimension ld) into the core-matrix layout: 16-byte unit (r, u)
-// (u = 8-column group) goes to (r / 8) * kSbo + u * 128 + (r % 8) * 16.
-__device__ __forceinline__ void stage(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int rows, int ld,
-                                      int k0, int kc) {
-    const int units = rows * (kc / 8);
-    for (int u = threadIdx.x; u < units; u += blockDim.x) {
-        const int r = u / (kc / 8), cu = u % (kc / 8);
-        const uint4 v = *reinterpret_cast<const uint4*>(src + (size_t)r * ld + k0 + cu * 8);
-        *reinterpret_cast<uint4*>(dst + (r / 8) * kSbo + cu * kCoreBytes + (r % 8) * 16) = v;
-    }
+// 2-D tiled bulk-tensor load (x = K column, y = row) into shared memory, completing on `bar`
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 2-D tiled bulk-tensor store of one box from shared memory (bulk-group completion)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
 // C = A * B^T for one tile: rows 128 blockIdx.x.., columns 64 blockIdx.y..; N a
-// multiple of 16 (<= 256), K a multiple of 16, M a multiple of 128.  *status != 0
-// after a timed-out wait.
-__global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __restrict__ A,
-                                                        const __nv_bfloat16* __restrict__ B, float* __restrict__ C,
-                                                        int M, int N, int K, uint32_t* status) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    // buffer b: A chunk at smem + b * kBufBytes, B chunk kABytes after it
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);  // one per buffer
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * kBufBytes + 16);
+// multiple of 16 (<= 256), K a multiple of 16, M a multiple of 128.  mapA / mapB
+// describe A [M x K] and B [N x K] (BF16, K innermost) with boxes of 8 K-columns
+// by 128 / 64 rows.  *status != 0 after a timed-out wait.
+__global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapB,
+                                                        const __grid_constant__ CUtensorMap mapC, int M, int N,
+                                                        int K, uint32_t* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // buffers start 1024-byte aligned: buffer b holds A at +0 and B at +kABytes, each as one box per 8 K-columns
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * kBufBytes);   // chunk landed, per buffer
+    uint64_t* done = full + 2;                                            // chunk's MMAs finished, per buffer
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
     __shared__ int s_fail;
     const int warp = threadIdx.x / 32;
     const int n0 = blockIdx.y * kCols;
@@ -149,8 +166,10 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __r
     const uint32_t ncols = nt <= 32 ? 32u : 64u;
     if (warp == 0) tmem_alloc(tslot, ncols);
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&done[b], 1);
+        }
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -159,57 +178,82 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16(const __nv_bfloat16* __r
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const int m0 = blockIdx.x * kRows;
-    const uint32_t idesc = instr_desc(kRows, nt);
     const int n_chunks = (K + kChunk - 1) / kChunk;
-    uint32_t phase0 = 0u, phase1 = 0u;  // parity of the next completion of each buffer's barrier
-    int committed = 0;  // chunks whose MMAs were issued
-    for (int c = 0; c < n_chunks; ++c) {
-        const int buf = c & 1;
-        if (c >= 2) {  // the MMAs of chunk c - 2 must be done reading this buffer
-            if (threadIdx.x == 0 && !mbar_wait(&bar[buf], buf ? phase1 : phase0)) s_fail = 1;
-            (buf ? phase1 : phase0) ^= 1u;
-            __syncthreads();
-            if (s_fail) break;
-        }
-        const int k0 = c * kChunk;
-        const int kc = (K - k0) < kChunk ? (K - k0) : kChunk;
-        unsigned char* sA = smem + buf * kBufBytes;
-        unsigned char* sB = sA + kABytes;
-        stage(sA, A + (size_t)m0 * K, kRows, K, k0, kc);
-        stage(sB, B + (size_t)n0 * K, nt, K, k0, kc);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy stores -> async proxy
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int ks = 0; ks < kc / 16; ++ks) {
-                const uint64_t da = smem_desc(smem_u32(sA) + ks * 2 * kCoreBytes, kCoreBytes, kSbo);
-                const uint64_t db = smem_desc(smem_u32(sB) + ks * 2 * kCoreBytes, kCoreBytes, kSbo);
-                mma_bf16(tmem, da, db, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = instr_desc(kRows, nt);
+        const uint32_t base = smem_u32(smem);
+        // stage chunk c into buffer c & 1 (its boxes beyond K are not loaded; rows beyond N read as zeros)
+        auto load = [&](int c) {
+            const int b = c & 1, k0 = c * kChunk;
+            const int groups = ((K - k0) < kChunk ? (K - k0) : kChunk) / 8;
+            mbar_expect_tx(&full[b], (uint32_t)groups * (kABox + kBBox));
+            for (int j = 0; j < groups; ++j) {
+                tma_load_2d(base + b * kBufBytes + j * kABox, &mapA, k0 + 8 * j, m0, &full[b]);
+                tma_load_2d(base + b * kBufBytes + kABytes + j * kBBox, &mapB, k0 + 8 * j, n0, &full[b]);
             }
-            mma_commit(&bar[buf]);
+        };
+        uint32_t ph_full0 = 0u, ph_full1 = 0u, ph_done0 = 0u, ph_done1 = 0u;  // parities of the next completions
+        auto wait = [&](uint64_t* bar, uint32_t& ph) {
+            const bool r = mbar_wait(bar, ph);
+            ph ^= 1u;
+            return r;
+        };
+        load(0);
+        if (n_chunks > 1) load(1);
+        bool ok = true;
+        for (int c = 0; c < n_chunks && ok; ++c) {
+            const int b = c & 1;
+            ok = wait(&full[b], b ? ph_full1 : ph_full0);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int kc = (K - c * kChunk) < kChunk ? (K - c * kChunk) : kChunk;
+            for (int ks = 0; ks < kc / 16; ++ks) {
+                const uint32_t a = base + b * kBufBytes + ks * 2 * kABox;
+                const uint32_t bb = base + b * kBufBytes + kABytes + ks * 2 * kBBox;
+                mma_bf16(tmem, smem_desc(a, kABox, kCoreBytes), smem_desc(bb, kBBox, kCoreBytes), idesc,
+                         (c > 0 || ks > 0) ? 1u : 0u);
+            }
+            mma_commit(&done[b]);
+            // chunk c + 1 goes into the other buffer once chunk c - 1's MMAs have read it (chunk 1: already loaded)
+            if (c >= 1 && c + 1 < n_chunks) {
+                ok = wait(&done[b ^ 1], b ? ph_done0 : ph_done1);
+                if (ok) load(c + 1);
+            }
         }
-        committed = c + 1;
+        // the last commits: every MMA has finished and the accumulator is complete
+        for (int c = n_chunks >= 2 ? n_chunks - 2 : 0; c < n_chunks && ok; ++c)
+            ok = wait(&done[c & 1], (c & 1) ? ph_done1 : ph_done0);
+        if (!ok) {
+            s_fail = 1;
+            // give copies and MMAs that may still be in flight a bounded time to land before the CTA exits
+            for (int b = 0; b < 2; ++b) {
+                (void)mbar_wait(&full[b], b ? ph_full1 : ph_full0, 1u << 16);
+                (void)mbar_wait(&done[b], b ? ph_done1 : ph_done0, 1u << 16);
+            }
+        }
     }
-    // the last (up to two) commits: every MMA has finished and the accumulator is complete
-    if (threadIdx.x == 0)
-        for (int c = committed >= 2 ? committed - 2 : 0; c < committed; ++c) {
-            const int buf = c & 1;
-            if (!mbar_wait(&bar[buf], buf ? phase1 : phase0)) s_fail = 1;
-            (buf ? phase1 : phase0) ^= 1u;
-        }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {
-        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+        // Epilogue: the tile goes through shared memory (the staging buffers are free now) as up to two boxes of
+        // 32 columns x 128 rows, each row 128 bytes with its 16-byte units XOR-swizzled by row % 8 (the TMA 128-byte
+        // swizzle, which also spreads a warp's stores over all banks), then one TMA store per box writes it out;
+        // columns beyond N are clipped by the tensor map.
+        const int r = warp * 32 + (threadIdx.x & 31);
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         for (int cb = 0; cb < nt; cb += 32) {
             float v[32];
             tmem_ld32(tmem + lane_base + (uint32_t)cb, v);
-            const int nv = (nt - cb) < 32 ? (nt - cb) : 32;
-            float* dst = C + (size_t)row * N + n0 + cb;
+            float4* box = reinterpret_cast<float4*>(smem + (cb / 32) * (kRows * 128) + r * 128);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < nv) dst[j] = v[j];
+            for (int j = 0; j < 8; ++j) box[j ^ (r & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy stores -> the TMA store
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int cb = 0; cb < nt; cb += 32) tma_store_2d(&mapC, n0 + cb, m0, smem_u32(smem) + (cb / 32) * (kRows * 128));
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory read before the CTA exits
         }
     } else if (threadIdx.x == 0) {
         atomicExch(status, 1u);
