@@ -48,6 +48,37 @@ def test_replicates_match_oracle_distribution(cuda, orc):
     assert ks.pvalue > 0.01, ks
 
 
+def test_whole_trajectories_match_oracle_distribution(cuda):
+    """Whole trajectories over the paper's horizon: 64 GPU replicates of the
+    benchmark protocol BMII (5 x 2 Gy daily from t = 0) for ten days (240 h,
+    144,000 steps) on 24^3 lattices, each growing its own seeded spheroid,
+    against the final counts of 64 oracle replicates drawn under another key
+    (tests/golden/replicates_240h.json, written from oracle/ alone by
+    make_replicates_golden.py): mean final count within 1 %, two-sample KS
+    p > 0.01."""
+    import json
+    import os
+    from paper_2303_08123_b300 import Simulator, csr
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "replicates_240h.json")) as f:
+        ref = json.load(f)
+    doses, waits = workloads.benchmark_bmii()
+    assert ref["doses"] == doses and ref["waits"] == waits
+    n, L, R, T = ref["n"], ref["L"], ref["R"], ref["hours"] * 600
+    sim = Simulator([L] * n, [R] * n, seed=0xA11CE, init_word=0xFFFFFFFE, t_end_steps=T)
+    sim.load_protocols(*csr([(doses, waits)] * n))
+    sim.autotune(3)
+    sim.run(0)
+    g, _ = sim.fitness()
+    o = np.array(ref["n_final"], dtype=np.float64)
+    assert np.std(g) > 0 and np.std(o) > 0
+    rel = abs(g.mean() - o.mean()) / o.mean()
+    ks = sps.ks_2samp(g, o)
+    print(f"whole trajectories: GPU mean {g.mean():.1f} sd {g.std():.1f}, oracle mean {o.mean():.1f} "
+          f"sd {o.std():.1f}, relative difference {rel:.4f}, KS p {ks.pvalue:.3f}")
+    assert rel < 0.01, (g.mean(), o.mean(), g.std(), o.std())
+    assert ks.pvalue > 0.01, ks
+
+
 @pytest.mark.parametrize("precision,field_tol,count_tol", [("bf16", 2.5e-2, 0.02), ("fp16", 5e-3, 0.01)])
 def test_reduced_precision_storage_against_oracle(cuda, orc, precision, field_tol, count_tol):
     from paper_2303_08123_b300 import Simulator, csr
