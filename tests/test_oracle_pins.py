@@ -669,3 +669,21 @@ def test_single_protocol_golden_was_written_by_this_oracle(orc):
     assert len(g["central_plane"]["O"]) == 40 * 40 and len(g["final_cells_sha256"]) == 64
     assert g["stats"]["n_near"] == 0 and g["stats"]["n_decisions"] > 10 ** 8
     assert sum(g["final_kind_histogram"]) == 40 ** 3 and g["cum_dose"] == 20.0
+
+
+def test_replicate_golden_was_written_by_this_oracle(orc):
+    """tests/golden/replicates_240h.json (64 oracle replicates of BMII over
+    240 h that the GPU's whole trajectories are compared with) is consistent
+    with the oracle as it stands: replicate 3 rerun for its first day gives the
+    stored day-1 count, and every replicate starts from the 515-cell ball."""
+    import json
+    import os
+    from synth import workloads
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "replicates_240h.json")) as f:
+        g = json.load(f)
+    doses, waits = workloads.benchmark_bmii()
+    assert g["doses"] == doses and g["waits"] == waits and len(g["n_final"]) == g["n"] == 64
+    daily = np.array(g["daily_counts"])
+    assert daily.shape == (64, 11) and np.all(daily[:, 0] == 515) and np.array_equal(daily[:, -1], g["n_final"])
+    ref = orc.run(P0, g["L"], g["R"], g["key"], 3, doses, waits, t_end_steps=24 * 600, hours=24, init_word=3)
+    assert int(ref["counts"][24]) == daily[3, 1]
