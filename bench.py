@@ -181,6 +181,13 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fused_passes(shape):
+    """Fused passes per CA step on a tile shape: passes of four substeps on the
+    deep TMA shapes (7, 8), of two elsewhere (the last one shorter)."""
+    depth = 4 if shape in (7, 8) else 2
+    return (PARAMS.n_sub + depth - 1) // depth, depth
+
+
 def traffic_for(kernel, n_sites):
     """DRAM bytes per launch from the committed ncu capture (64 protocols of
     64^3; bytes per site scaled to the batch's sites), or None when a kernel
@@ -345,7 +352,7 @@ def run_ours(args):
     protocol_steps_per_s = world * N_PROT * STEPS_PER_HOUR * K / (ms / 1e3)
     value = protocol_steps_per_s / (mean_h * STEPS_PER_HOUR)
     site_steps_per_s = world * sites * STEPS_PER_HOUR * K / (ms / 1e3)
-    per_ca_step = ((PARAMS.n_sub + 1) // 2 + 2) if args.path == "fused" else (PARAMS.n_sub + 3)
+    per_ca_step = (fused_passes(shape)[0] + 2) if args.path == "fused" else (PARAMS.n_sub + 3)
     launches_per_step = STEPS_PER_HOUR * per_ca_step + 2  # passes (or substeps + cell), claim, resolve; tick, count
 
     # per-kernel device time over plain steps of the same batch (CUDA events on the launching stream)
@@ -353,12 +360,21 @@ def run_ours(args):
     interior = float(np.sum((Ls.astype(np.float64) - 2) ** 3))
     es = 4 if args.precision == "fp32" else 2
     if args.path == "fused":
-        kn = ("k_tma" if shape in (5, 6) else
+        kn = ("k_tma" if shape in (5, 6, 7, 8) else
               ("k_fused1" if args.precision == "fp32" else "k_fused1h") if shape in (3, 4) else "k_fused")
-        classes = {f"{kn} (first pass: irradiation + 2 substeps)": (kms[0], kl[0], interior * (6 * es + 4)),
-                   f"{kn} (last pass: 2 substeps + cell update)": (kms[1], kl[1], interior * (6 * es + 8))}
-        traffic_key = {f"{kn} (first pass: irradiation + 2 substeps)": f"{kn}_first_shape{shape}",
-                       f"{kn} (last pass: 2 substeps + cell update)": f"{kn}_last_shape{shape}"}
+        n_pass, depth = fused_passes(shape)
+        k_last = PARAMS.n_sub - depth * (n_pass - 1)
+        if n_pass == 1:
+            last = f"{kn} (one pass per step: irradiation + {k_last} substeps + cell update)"
+            classes = {last: (kms[1], kl[1], interior * (6 * es + 8))}
+            traffic_key = {last: f"{kn}_last_shape{shape}"}
+        else:
+            first = f"{kn} (first pass: irradiation + {depth} substeps)" if n_pass == 2 else \
+                f"{kn} (passes before the last: {depth} substeps each, irradiation in the first)"
+            last = f"{kn} (last pass: {k_last} substeps + cell update)"
+            classes = {first: (kms[0], kl[0], interior * (6 * es + 4)),
+                       last: (kms[1], kl[1], interior * (6 * es + 8))}
+            traffic_key = {first: f"{kn}_first_shape{shape}", last: f"{kn}_last_shape{shape}"}
     else:
         classes = {"k_substep": (kms[0], kl[0], interior * (6 * es + 4)),
                    "k_cell": (kms[1], kl[1], interior * (3 * es + 8))}
@@ -472,7 +488,7 @@ def full_run(args, sim, prot, mean_h, Ls, shape, shape_ms, world, rank, dev, bar
                 "site_updates_per_s": world * site_steps / (ms / 1e3),
                 "final_count_mean": float(np.mean(cnt)),
                 # every CA step: the fused passes, claim, resolve; every hour: clock tick and count; then fitness
-                "gpu_launches": int(STEPS_PER_HOUR * horizons.max() * (((PARAMS.n_sub + 1) // 2 + 2)
+                "gpu_launches": int(STEPS_PER_HOUR * horizons.max() * ((fused_passes(shape)[0] + 2)
                                                                        if args.path == "fused" else PARAMS.n_sub + 3)
                                     + 2 * int(np.ceil(horizons.max())) + 1),
                 "clocks": clk.summary()}
@@ -490,7 +506,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "substep"])
-    ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-6 (0: autotune)")
+    ap.add_argument("--tile-shape", type=int, default=0, help="fused tile shape 1-8 (0: autotune)")
     ap.add_argument("--z-chunk", type=int, default=0, help="planes per fused CTA (0: split to fill the GPU)")
     ap.add_argument("--workload", default="ragged", choices=["ga_batch", "ragged", "single"],
                     help="ragged: 1,024 protocols on 32^3-112^3 (default); ga_batch: 256 x 64^3; "

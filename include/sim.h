@@ -89,8 +89,10 @@ typedef struct {
                                thread (packed FP32); 3 = 32 x 16, 4 = 16 x 16 with one column per
                                thread; 5 = 32 x 16, 6 = 16 x 16 with one column per thread and the
                                planes staged by TMA (FP32 storage, every lattice side a multiple of
-                               4).  For a given storage precision every shape gives the same
-                               results bit for bit */
+                               4); 7 = 32 x 16, 8 = 16 x 16 as 5 and 6 with passes of four
+                               substeps instead of two (n_sub even; the last pass two deep when
+                               n_sub is not a multiple of 4).  For a given storage precision every
+                               shape gives the same results bit for bit */
     int32_t z_chunk;        /* fused z range per CTA: 0 auto, else planes per CTA */
 } sim_config;
 
@@ -261,12 +263,12 @@ sim_status sim_diffuse_noalloc(const sim_config* cfg, int L, int64_t step, doubl
 
 /*
  * Autotuner of the fused path: time n_steps plain steps of this context's own
- * batch with every applicable tile shape (sim_config.tile_shape 1..6) -- on a
+ * batch with every applicable tile shape (sim_config.tile_shape 1..8) -- on a
  * batch with too few column tiles to fill the GPU (split in z unless
  * sim_config.z_chunk fixes the split) each shape also with a finer z split of
  * 2 planes per CTA -- keep the fastest, then re-seed every spheroid and set the
  * clock to 0 (call it right after sim_load_protocols).  *best (may be NULL)
- * receives the chosen shape (0 on the substep path); ms (6 entries, may be
+ * receives the chosen shape (0 on the substep path); ms (8 entries, may be
  * NULL) the device milliseconds per step of each shape (its faster split), -1
  * where a shape does not apply.  Synchronises.
  */

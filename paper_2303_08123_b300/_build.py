@@ -34,9 +34,10 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False) -> list:
+    """Compile every stale library; the nvcc runs proceed in parallel."""
     os.makedirs(LIBDIR, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _deps())
-    out = []
+    out, jobs = [], []
     for lib, (srcs, flags) in TARGETS.items():
         dst = os.path.join(LIBDIR, lib)
         out.append(dst)
@@ -49,8 +50,17 @@ def build(force: bool = False, verbose: bool = False) -> list:
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
-        os.replace(tmp, dst)
+        jobs.append((subprocess.Popen(cmd), cmd, tmp, dst))
+    failed = None
+    for proc, cmd, tmp, dst in jobs:
+        if proc.wait() != 0:
+            failed = failed or subprocess.CalledProcessError(proc.returncode, cmd)
+            if os.path.exists(tmp):
+                os.remove(tmp)
+        else:
+            os.replace(tmp, dst)
+    if failed:
+        raise failed
     return out
 
 

@@ -39,7 +39,7 @@ struct Layout {
         clock, status, final_count, first_block, part64, part32, tot64, tot32, tile_ctr, tmaps, total;
 };
 
-constexpr int kTmaShapes = 2;  // tile shapes 5 and 6 stage their planes by TMA (one set of tensor maps each)
+constexpr int kTmaShapes = 4;  // tile shapes 5-8 stage their planes by TMA (one set of tensor maps each)
 
 // Number of distinct lattice sides (one set of tensor maps each).
 int side_classes(int n, const int32_t* L) {
@@ -105,17 +105,22 @@ bool valid_config(const sim_config* cfg, std::string* why) {
         return *why = "repair_half_h must be finite and >= 0", false;
     if (cfg->regrowth_h < 0) return *why = "regrowth_h must be >= 0", false;
     if (cfg->path < SIM_PATH_FUSED || cfg->path > SIM_PATH_SUBSTEP) return *why = "unknown kernel path", false;
-    if (cfg->tile_shape < 0 || cfg->tile_shape > 6) return *why = "tile_shape must be in 0..6", false;
+    if (cfg->tile_shape < 0 || cfg->tile_shape > 8) return *why = "tile_shape must be in 0..8", false;
     if (cfg->z_chunk < 0) return *why = "z_chunk must be >= 0", false;
     return true;
 }
 
 // Tile shapes of the fused kernels: (x extent, y extent); shapes 1-2 run two
 // columns per thread (packed f32x2), shapes 3-4 one column per thread, shapes
-// 5-6 one column per thread with the planes staged by TMA (FP32 storage).
-constexpr int kNumShapes = 6;
-constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0}, {32, 16}, {16, 16}, {32, 16}, {16, 16}, {32, 16}, {16, 16}};
-bool tma_shape(int sh) { return sh == 5 || sh == 6; }
+// 5-6 one column per thread with the planes staged by TMA (FP32 storage),
+// shapes 7-8 the same with passes of four substeps (deep temporal blocking;
+// an even substep count, the last pass two deep when it is not a multiple of 4).
+constexpr int kNumShapes = 8;
+constexpr int kTileShapes[kNumShapes + 1][2] = {{0, 0},   {32, 16}, {16, 16}, {32, 16}, {16, 16},
+                                                {32, 16}, {16, 16}, {32, 16}, {16, 16}};
+bool tma_shape(int sh) { return sh >= 5 && sh <= 8; }
+bool deep_shape(int sh) { return sh == 7 || sh == 8; }
+int tma_halo_y(int sh) { return deep_shape(sh) ? 4 : 2; }  // rows of halo in the staged box
 
 // First site of each protocol: the running total rounded up to a multiple of
 // L^2, so that a protocol's planes are whole z-slices of the L x L x Z volume a
@@ -222,7 +227,7 @@ struct sim_ctx {
     int64_t counted_hour = -1;  // last hour whose counts were recorded
     bool loaded = false;
     cudaGraphExec_t hour_graph[4] = {nullptr, nullptr, nullptr, nullptr};  // by (field, cell) start buffers
-    bool tma_ok = false;  // tensor maps encoded: shapes 5 and 6 may run
+    bool tma_ok = false;  // tensor maps encoded: shapes 5-8 may run
     int n_sides = 0;      // distinct lattice sides (tensor-map classes)
     std::string err;
 
@@ -231,9 +236,10 @@ struct sim_ctx {
     void* field(int buf, int f) const { return ws + lay.field[buf][f]; }
     uint32_t* cells(int buf) const { return reinterpret_cast<uint32_t*>(ws + lay.cell[buf]); }
     bool fused() const { return cfg.path == SIM_PATH_FUSED; }
-    // substeps per fused pass: passes of two, one pass of one for an odd remainder
-    int passes() const { return (P.n_sub + 1) / 2; }
-    int pass_k(int j) const { return (j == passes() - 1 && (P.n_sub & 1)) ? 1 : 2; }
+    // substeps per fused pass: passes of two (of four on the deep shapes), the last one shorter by the remainder
+    int depth() const { return deep_shape(shape) ? 4 : 2; }
+    int passes() const { return (P.n_sub + depth() - 1) / depth(); }
+    int pass_k(int j) const { return j < passes() - 1 ? depth() : P.n_sub - depth() * (passes() - 1); }
     int field_flips() const { return fused() ? passes() : P.n_sub; }
     int cell_flips() const { return fused() ? 1 : 0; }
 };
@@ -370,16 +376,17 @@ void launch_fused1_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, 
         launch_fused1_f<T, TX, TY, K, EPI, false>(c, s, k_off, first, buf, cin, cout, pass);
 }
 
-template <int TX, int TY, int K, bool EPI, bool FULL>
+template <int TX, int TY, int K, int HY, bool EPI, bool FULL>
 void launch_tma_f(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, int cbuf, uint32_t* cout, int pass) {
-    using Sh = TmaShape<TX, TY, K>;
-    constexpr auto kern = k_tma<TX, TY, K, EPI, FULL>;
+    using Sh = TmaShape<TX, TY, K, HY>;
+    constexpr auto kern = k_tma<TX, TY, K, HY, EPI, FULL>;
+    constexpr size_t smem = tma_smem_bytes<TX, TY, K, HY>();
     static unsigned grid = 0;
-    if (!grid) grid = persistent_grid(kern, Sh::THREADS, tma_smem_bytes<TX, TY, K>(), ~0ull);
+    if (!grid) grid = persistent_grid(kern, Sh::THREADS, smem, ~0ull);
     const unsigned g = grid < c->tiles.size() ? grid : (unsigned)c->tiles.size();
     const CUtensorMap* maps =
         c->at<CUtensorMap>(c->lay.tmaps) + (size_t)(c->shape - 5) * c->n_sides * kTmaArrays;
-    kern<<<g, Sh::THREADS, tma_smem_bytes<TX, TY, K>(), s>>>(
+    kern<<<g, Sh::THREADS, smem, s>>>(
         c->at<Tile>(c->lay.tiles), c->at<Proto>(c->lay.proto), c->at<int64_t>(c->lay.clock), k_off, first, maps,
         3 * buf, (float*)c->field(buf ^ 1, 0), (float*)c->field(buf ^ 1, 1), (float*)c->field(buf ^ 1, 2), 6 + cbuf,
         cout, c->at<int64_t>(c->lay.fstep), c->at<double>(c->lay.fdose), c->at<double>(c->lay.cum),
@@ -387,22 +394,34 @@ void launch_tma_f(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, int
         (int)c->tiles.size(), pass, c->P);
 }
 
-template <int TX, int TY, int K, bool EPI>
+template <int TX, int TY, int K, int HY, bool EPI>
 void launch_tma_t(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
                   int pass) {
     const int cbuf = cin == c->cells(0) ? 0 : 1;
     if ((c->P.flags & (kFDiffusion | kFReaction)) == (kFDiffusion | kFReaction))
-        launch_tma_f<TX, TY, K, EPI, true>(c, s, k_off, first, buf, cbuf, cout, pass);
+        launch_tma_f<TX, TY, K, HY, EPI, true>(c, s, k_off, first, buf, cbuf, cout, pass);
     else
-        launch_tma_f<TX, TY, K, EPI, false>(c, s, k_off, first, buf, cbuf, cout, pass);
+        launch_tma_f<TX, TY, K, HY, EPI, false>(c, s, k_off, first, buf, cbuf, cout, pass);
+}
+
+// a pass of four substeps: the deep TMA shapes only
+template <bool EPI>
+void launch_deep(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
+                 int pass) {
+    if (c->shape == 7) launch_tma_t<32, 16, 4, 4, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+    else launch_tma_t<16, 16, 4, 4, EPI>(c, s, k_off, first, buf, cin, cout, pass);
 }
 
 template <typename T, int K, bool EPI>
 void launch_fused_k(sim_ctx* c, cudaStream_t s, int k_off, int first, int buf, const uint32_t* cin, uint32_t* cout,
                     int pass) {
     if constexpr (std::is_same<T, float>::value) {  // TMA staging: FP32 storage only
-        if (c->shape == 5) return launch_tma_t<32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
-        if (c->shape == 6) return launch_tma_t<16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+        if (c->shape == 5) return launch_tma_t<32, 16, K, 2, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+        if (c->shape == 6) return launch_tma_t<16, 16, K, 2, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+        if constexpr (K == 2) {  // the two-substep remainder pass of a deep shape
+            if (c->shape == 7) return launch_tma_t<32, 16, 2, 4, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+            if (c->shape == 8) return launch_tma_t<16, 16, 2, 4, EPI>(c, s, k_off, first, buf, cin, cout, pass);
+        }
     }
     if (c->shape == 3) return launch_fused1_t<T, 32, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
     if (c->shape == 4) return launch_fused1_t<T, 16, 16, K, EPI>(c, s, k_off, first, buf, cin, cout, pass);
@@ -450,22 +469,24 @@ cudaError_t fused1_attrs_shape() {
     return e;
 }
 
-template <int TX, int TY, int K, bool FULL>
+template <int TX, int TY, int K, int HY, bool FULL>
 cudaError_t tma_attrs_k() {
-    cudaError_t e = cudaFuncSetAttribute(k_tma<TX, TY, K, false, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tma_smem_bytes<TX, TY, K>());
+    constexpr int smem = (int)tma_smem_bytes<TX, TY, K, HY>();
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tma<TX, TY, K, HY, false, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (!e)
-        e = cudaFuncSetAttribute(k_tma<TX, TY, K, true, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_smem_bytes<TX, TY, K>());
+        e = cudaFuncSetAttribute(k_tma<TX, TY, K, HY, true, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
-template <int TX, int TY>
+// the pass depths a shape runs: 1 and 2 on the two-row halo, 2 and 4 on the deep (four-row) one
+template <int TX, int TY, int HY>
 cudaError_t tma_attrs_shape() {
-    cudaError_t e = tma_attrs_k<TX, TY, 1, true>();
-    if (!e) e = tma_attrs_k<TX, TY, 2, true>();
-    if (!e) e = tma_attrs_k<TX, TY, 1, false>();
-    if (!e) e = tma_attrs_k<TX, TY, 2, false>();
+    constexpr int K0 = HY > 2 ? 2 : 1, K1 = HY > 2 ? 4 : 2;
+    cudaError_t e = tma_attrs_k<TX, TY, K0, HY, true>();
+    if (!e) e = tma_attrs_k<TX, TY, K1, HY, true>();
+    if (!e) e = tma_attrs_k<TX, TY, K0, HY, false>();
+    if (!e) e = tma_attrs_k<TX, TY, K1, HY, false>();
     return e;
 }
 
@@ -476,16 +497,19 @@ cudaError_t fused_attrs() {
     if (!e) e = fused1_attrs_shape<T, 32, 16>();
     if (!e) e = fused1_attrs_shape<T, 16, 16>();
     if constexpr (std::is_same<T, float>::value) {
-        if (!e) e = tma_attrs_shape<32, 16>();
-        if (!e) e = tma_attrs_shape<16, 16>();
+        if (!e) e = tma_attrs_shape<32, 16, 2>();
+        if (!e) e = tma_attrs_shape<16, 16, 2>();
+        if (!e) e = tma_attrs_shape<32, 16, 4>();
+        if (!e) e = tma_attrs_shape<16, 16, 4>();
     }
     return e;
 }
 
-// Tensor maps of the TMA-staged passes: per tile shape (5, 6), lattice-side
+// Tensor maps of the TMA-staged passes: per tile shape (5-8), lattice-side
 // class and array (O, G, H of both field buffers, both cell-word buffers), an
 // L x L x Z volume over the whole array (Z = planes of L^2 sites it spans) with
-// a (TX + 8) x (TY + 4) x 1 box; sites outside the volume read as zero.  The
+// a (TX + 8) x (TY + 2 HY) x 1 box (HY = 2, or 4 on the deep shapes); sites
+// outside the volume read as zero.  The
 // encoder is the driver's, reached through the runtime so that the library
 // links against the runtime only.  False if any map cannot be encoded (the TMA
 // shapes are then unavailable).
@@ -507,7 +531,8 @@ bool encode_tensor_maps(sim_ctx* c, const std::vector<int32_t>& sides) {
             const cuuint64_t Lk = (cuuint64_t)sides[k];
             const cuuint64_t dims[3] = {Lk, Lk, (cuuint64_t)c->total_sites / (Lk * Lk)};
             const cuuint64_t strides[2] = {Lk * 4, Lk * Lk * 4};  // bytes, dimensions 1 and 2
-            const cuuint32_t box[3] = {(cuuint32_t)(TX + 2 * kTmaHaloX), (cuuint32_t)(TY + 2 * kTmaHaloY), 1};
+            const cuuint32_t box[3] = {(cuuint32_t)(TX + 2 * kTmaHaloX), (cuuint32_t)(TY + 2 * tma_halo_y(5 + sh)),
+                                       1};
             const cuuint32_t estr[3] = {1, 1, 1};
             for (int a = 0; a < kTmaArrays; ++a) {
                 void* base = a < 6 ? c->field(a / 3, a % 3) : (void*)c->cells(a - 6);
@@ -533,6 +558,9 @@ void launch_fused(sim_ctx* c, cudaStream_t s, int k_off, int K, bool epi, int fi
     if (K == 1) {
         if (epi) launch_fused_k<T, 1, true>(c, s, k_off, first, buf, cin, cout, pass);
         else launch_fused_k<T, 1, false>(c, s, k_off, first, buf, cin, cout, pass);
+    } else if (K == 4) {
+        if (epi) launch_deep<true>(c, s, k_off, first, buf, cin, cout, pass);
+        else launch_deep<false>(c, s, k_off, first, buf, cin, cout, pass);
     } else {
         if (epi) launch_fused_k<T, 2, true>(c, s, k_off, first, buf, cin, cout, pass);
         else launch_fused_k<T, 2, false>(c, s, k_off, first, buf, cin, cout, pass);
@@ -882,7 +910,9 @@ sim_status sim_create(const sim_config* cfg, int n, const int32_t* L, const int3
     // without the autotuner a 16 x 16 one-column context runs the TMA-staged kernel of the same tiles
     if (!st && cfg->tile_shape == 0 && c->tma_ok && c->shape == 4) c->shape = 6;
     if (!st && c->cfg.path == SIM_PATH_FUSED && tma_shape(c->shape) && !c->tma_ok)
-        st = fail(c, SIM_EINVAL, "tile shapes 5 and 6 need FP32 storage and lattice sides that are multiples of 4");
+        st = fail(c, SIM_EINVAL, "tile shapes 5-8 need FP32 storage and lattice sides that are multiples of 4");
+    if (!st && c->cfg.path == SIM_PATH_FUSED && deep_shape(c->shape) && (c->P.n_sub & 1))
+        st = fail(c, SIM_EINVAL, "tile shapes 7 and 8 run passes of four and two substeps: n_sub must be even");
     if (!st) st = reset_device(c);
     if (st) {
         delete c;
@@ -1100,6 +1130,7 @@ sim_status sim_autotune(sim_ctx* c, int n_steps, int* best, double* ms) {
     for (int sh = 1; sh <= kNumShapes && st == SIM_OK; ++sh)
         for (int fz : {0, kFineZ}) {
             if (tma_shape(sh) && !c->tma_ok) continue;
+            if (deep_shape(sh) && (c->P.n_sub & 1)) continue;
             if (fz && !z_split_applies(c->cfg, c->n, L.data(), sh)) continue;
             c->fine_z = fz;
             st = set_shape(c, sh, L);

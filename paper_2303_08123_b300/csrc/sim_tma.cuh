@@ -9,9 +9,11 @@
 //     shared-memory stages; each stage completes on its own mbarrier
 //     (expect-tx bytes), and every thread waits on it with a bounded spin;
 //   * the box starts 4 columns left of the tile (a 16-byte aligned x
-//     coordinate) and 2 rows above it; rows, columns and planes outside the
-//     lattice arrive as zeros, which is what the cell-word and field halo of a
-//     lattice edge needs (such sites are faces and never feed an interior site);
+//     coordinate) and HY rows above it (HY = 2 for passes of up to two
+//     substeps, 4 for the deep shapes' passes of up to four); rows, columns and
+//     planes outside the lattice arrive as zeros, which is what the cell-word
+//     and field halo of a lattice edge needs (such sites are faces and never
+//     feed an interior site);
 //   * the thread grid covers only the level-1 region (the tile plus K - 1
 //     columns), not the outer halo the copies used to need a thread for.
 // One tensor map per (lattice side, array, tile shape) addresses each array as
@@ -28,27 +30,27 @@ namespace simdev {
 
 constexpr int kTmaArrays = 8;        // tensor maps per (side, shape): O0, G0, H0, O1, G1, H1, C0, C1
 constexpr int kTmaHaloX = 4;         // box x origin: 4 columns left of the tile (x * 4 B stays 16-byte aligned)
-constexpr int kTmaHaloY = 2;         // box y origin: 2 rows above the tile (the deepest halo of a pass)
 constexpr int kTmaStages = 8;        // shared-memory stages (a power of two >= kDepth + 2)
 constexpr uint32_t kStatusTmaTimeout = 8u;  // a stage's copies did not land within the bounded wait
 
-template <int TX, int TY, int K>
+// HY: rows of halo the staged box carries above and below the tile (the deepest pass it serves)
+template <int TX, int TY, int K, int HY>
 struct TmaShape {
     static constexpr int BX = TX + 2 * kTmaHaloX;  // staged box (x extent)
-    static constexpr int BY = TY + 2 * kTmaHaloY;  // staged box (y extent)
+    static constexpr int BY = TY + 2 * HY;         // staged box (y extent)
     static constexpr int NB = BX * BY;             // sites of one staged plane
     static constexpr int RX = TX + 2 * (K - 1);    // level-1 region = thread grid
     static constexpr int RY = TY + 2 * (K - 1);
     static constexpr int NR = RX * RY;
     static constexpr int THREADS = (NR + 31) / 32 * 32;
     static_assert((NB * 4) % 128 == 0, "every staged array must start 128-byte aligned");
-    static_assert(K >= 1 && K <= kTmaHaloY, "the box carries a halo of at most two rows");
+    static_assert(K >= 1 && K <= HY && K <= kTmaHaloX, "a pass of K substeps needs a box halo of K sites");
 };
 
 // dynamic shared memory: stages (4 planar arrays each) + level planes (float2 O2/glucose, float H+) + alignment slack
-template <int TX, int TY, int K>
+template <int TX, int TY, int K, int HY>
 constexpr size_t tma_smem_bytes() {
-    using S = TmaShape<TX, TY, K>;
+    using S = TmaShape<TX, TY, K, HY>;
     return 128 + (size_t)kTmaStages * 4 * S::NB * sizeof(float) +
            (size_t)((K > 1) ? K - 1 : 1) * 2 * S::NR * (sizeof(float2) + sizeof(float));
 }
@@ -95,18 +97,22 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 #ifndef SIM_TMA_MIN_BLOCKS_SMALL
 #define SIM_TMA_MIN_BLOCKS_SMALL 2  // CTAs per SM the 16 x 16 TMA kernel is register-budgeted for
 #endif
+#ifndef SIM_TMA_MIN_BLOCKS_DEEP
+#define SIM_TMA_MIN_BLOCKS_DEEP 1  // the same for its passes of four substeps
+#endif
 
 // FULL: diffusion and reaction both on (the model as run), so their switches
 // are compile-time constants; other switch settings run the FULL = false instance.
-template <int TX, int TY, int K, bool EPI, bool FULL>
-__global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256) ? SIM_TMA_MIN_BLOCKS_SMALL : 1)
+template <int TX, int TY, int K, int HY, bool EPI, bool FULL>
+__global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
+                                  (TX * TY > 256) ? 1 : (K > 2 ? SIM_TMA_MIN_BLOCKS_DEEP : SIM_TMA_MIN_BLOCKS_SMALL))
     k_tma(const Tile* __restrict__ tiles, const Proto* __restrict__ protos, const int64_t* __restrict__ clock,
           int k_off, int first, const CUtensorMap* __restrict__ maps, int map_in, float* __restrict__ oO,
           float* __restrict__ oG, float* __restrict__ oH, int map_cin, uint32_t* cout,
           const int64_t* __restrict__ fstep, const double* __restrict__ fdose, double* __restrict__ cum_dose,
           uint32_t* __restrict__ intents, uint32_t* __restrict__ icount, uint32_t* __restrict__ tile_ctr, int n_tiles,
           int pass, Params P) {
-    using S = TmaShape<TX, TY, K>;
+    using S = TmaShape<TX, TY, K, HY>;
     constexpr int BX = S::BX, NB = S::NB, RX = S::RX, RY = S::RY, NR = S::NR;
     constexpr int kS = kTmaStages;
     constexpr uint32_t kStageBytes = 4u * NB * sizeof(float);
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
     for (int l = 1; l <= K; ++l) inreg[l] = act && rx >= l - 1 && rx < RX - (l - 1) && ry >= l - 1 && ry < RY - (l - 1);
     const bool outtile = inreg[K];
     // this thread's site in a staged plane
-    const int sb = (ry + kTmaHaloY - (K - 1)) * BX + (rx + kTmaHaloX - (K - 1));
+    const int sb = (ry + HY - (K - 1)) * BX + (rx + kTmaHaloX - (K - 1));
     float2* const my_lvog = lv_og + tid;  // + ((l - 1) * 2 + parity) * NR
     float* const my_lvh = lv_h + tid;
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
     // tensor maps of this protocol's lattice side; the protocol's planes start at z = site0 / L^2
     const CUtensorMap* mf = maps + (size_t)pr.tmap * kTmaArrays;
     const int zb = (int)(pr.site0 / LL);
-    const int bx0 = tl.x0 - kTmaHaloX, by0 = tl.y0 - kTmaHaloY;
+    const int bx0 = tl.x0 - kTmaHaloX, by0 = tl.y0 - HY;
     const uint32_t g0 = loaded_planes;
 
     // thread 0 stages level-0 plane j (all four arrays) into its ring slot
@@ -200,8 +206,15 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
             rog[l][j] = f2(0.f, 0.f);
             rh[l][j] = 0.f;
         }
-    uint32_t wr[3] = {0u, 0u, 0u};
-    uint32_t hit = 0;
+    // cell words of the planes in flight: while a pass is at most two substeps deep, planes i, i - 1 and
+    // i - 2 fit one ring of three; a deeper pass hands each plane's word on from level to level
+    constexpr int kWr = (K <= 2) ? 1 : K;
+    uint32_t wr[kWr][3];
+#pragma unroll
+    for (int l = 0; l < kWr; ++l)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) wr[l][j] = 0u;
+    uint32_t hit = 0;  // planes whose word irradiation changed (passes of at most two substeps)
 
 #pragma unroll
     for (int j = 0; j < kDepth; ++j) issue(zl0 + j);
@@ -242,13 +255,17 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
                 w = nw;
             }
         }
-        wr[ph] = w;
+        wr[0][ph] = w;
         rog[0][ph] = v0og;
         rh[0][ph] = v0h;
 #pragma unroll
         for (int l = 1; l <= K; ++l) {
             const int q = i - l;
             const int sq = (ph - l + 6) % 3, sm = (ph - l - 1 + 6) % 3, sp = (ph - l + 1 + 6) % 3;
+            const uint32_t wq = wr[(K <= 2) ? 0 : l - 1][sq];  // the cell word of plane q
+            if constexpr (K > 2) {
+                if (l < K) wr[l][sq] = wq;
+            }
             bool reg = inreg[l];
             if constexpr (CHK) {
                 const int lo = (zl0 == 0) ? 0 : zl0 + l;
@@ -297,7 +314,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
                         vh = ch;
                     }
                     float uO = 0.f, uG = 0.f, pHv = 0.f;
-                    const uint32_t kq = wr[sq] & kKindMask;
+                    const uint32_t kq = wq & kKindMask;
                     if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
                     const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));  // v - u, lane by lane
                     vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
@@ -322,11 +339,12 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K>::THREADS, (TX * TY <= 256)
                         d1[o] = vog.y;
                         d2[o] = vh;
                     }
-                    const uint32_t w0 = wr[sq];
+                    const uint32_t w0 = wq;
+                    // only irradiation changes words here; a deeper pass stores every word of a dose step
                     if (EPI) dC[o] = face ? w0 : update_cell(w0, vog.x, vog.y, vh, P, want);
-                    else if (dose > 0.f && (hit >> sq & 1u)) dC[o] = w0;  // only irradiation changes words here
+                    else if (dose > 0.f && (K > 2 || (hit >> sq & 1u))) dC[o] = w0;
                 }
-                if (!EPI && dose > 0.f) hit &= ~(1u << sq);
+                if (K <= 2 && !EPI && dose > 0.f) hit &= ~(1u << sq);
                 if (EPI) {
                     const uint32_t mask = __ballot_sync(0xffffffffu, want);
                     if (mask) {

@@ -297,7 +297,7 @@ class Simulator:
         """Time every fused tile shape on this batch, keep the fastest and re-seed
         the batch at step 0.  Returns (best shape, ms per step per shape)."""
         best = ctypes.c_int(0)
-        ms = np.full(6, -1.0)
+        ms = np.full(8, -1.0)
         self._call("sim_autotune", int(n_steps), ctypes.byref(best), _ptr(ms, ctypes.c_double))
         return best.value, ms
 

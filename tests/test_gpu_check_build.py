@@ -20,7 +20,7 @@ def cuda():
 
 
 @pytest.mark.parametrize("path,shape", [("fused", 3), ("fused", 4), ("fused", 1), ("fused", 5), ("fused", 6),
-                                        ("substep", 0)])
+                                        ("fused", 7), ("fused", 8), ("substep", 0)])
 def test_checked_build_stays_in_bounds_and_matches(cuda, path, shape):
     from paper_2303_08123_b300 import Simulator, csr
     from synth import workloads

@@ -235,13 +235,16 @@ def test_fused_path_equals_substep_path(cuda, shape, zc):
 
 
 @pytest.mark.parametrize("shape,zc,n_sub", [(5, 0, 4), (6, 0, 4), (5, 11, 4), (6, 9, 3), (5, 0, 1), (6, 13, 1),
-                                            (6, 2, 4), (5, 2, 3)])
+                                            (6, 2, 4), (5, 2, 3), (7, 0, 4), (8, 0, 4), (7, 11, 4), (8, 9, 6),
+                                            (8, 0, 2), (7, 2, 8), (8, 2, 6), (8, 5, 12)])
 def test_tma_staged_path_equals_substep_path(cuda, shape, zc, n_sub):
     """The TMA-staged passes (tile shapes 5 and 6: bulk-tensor loads of the
-    planes, threads over the level-1 region only) reproduce the substep path
-    bit for bit in FP32, with z splits, an odd substep count and passes of one
-    substep; lattice sides 24-48 (multiples of 4) so that tiles overhang the
-    lattice on every side."""
+    planes, threads over the level-1 region only; 7 and 8: the same with passes
+    of four substeps, one pass per step at n_sub = 4, a two-deep remainder
+    pass at n_sub = 6) reproduce the substep path bit for bit in FP32, with z
+    splits (down to 2 planes per CTA, below the deep pass's halo of 4), an odd
+    substep count and passes of one substep; lattice sides 24-48 (multiples of
+    4) so that tiles overhang the lattice on every side."""
     from paper_2303_08123_b300 import csr
     from synth import workloads
     L, R = [40, 24, 32, 48], [6, 5, 4, 7]
@@ -269,13 +272,21 @@ def test_tma_shapes_need_sides_that_are_multiples_of_four(cuda):
         _sim([40], [5], tile_shape=6, precision="bf16")
 
 
-@pytest.mark.parametrize("n_sub", [1, 3, 4])
-def test_fused_pass_split_matches_oracle(cuda, orc, n_sub):
-    """n_sub split into fused passes of two (and one) substeps: one step from a
-    crowded state against the oracle."""
+def test_deep_shapes_need_an_even_substep_count(cuda):
+    from paper_2303_08123_b300 import SimError
+    for shape in (7, 8):
+        with pytest.raises(SimError):
+            _sim([40], [5], tile_shape=shape, params=P0.replace(n_sub=3))
+
+
+@pytest.mark.parametrize("n_sub,shape", [(1, 0), (3, 0), (4, 0), (4, 8), (6, 7), (2, 8), (8, 8)])
+def test_fused_pass_split_matches_oracle(cuda, orc, n_sub, shape):
+    """n_sub split into fused passes of two (and one) substeps, or of four
+    (and two) on the deep shapes: one step from a crowded state against the
+    oracle."""
     L, step = 24, 900
     p = P0.replace(n_sub=n_sub)
-    sim = _sim([L], [-1], params=p)
+    sim = _sim([L], [-1], params=p, tile_shape=shape)
     _load_single_fraction(sim, step, [2.0])
     fields, cell = par.random_state(L, 31)
     sim.set_state(0, *fields, cell)
@@ -297,7 +308,7 @@ def test_autotune_picks_a_shape_and_restarts_the_batch(cuda):
     sim = _sim(L, R, hours=1, t_end_steps=900)
     sim.load_protocols(*prot)
     best, ms = sim.autotune(3)
-    assert best in range(1, 7) and ms[best - 1] == ms[ms > 0].min()
+    assert best in range(1, 9) and ms[best - 1] == ms[ms > 0].min()
     assert np.all(ms > 0)  # FP32, sides multiples of 4: every shape applies, the TMA-staged ones included
     assert sim.clock()[0][0] == 0
     sim.run(0)
@@ -418,22 +429,25 @@ def test_incomplete_repair_parity(cuda, orc, path):
 
 def test_physical_rate_variant(cuda, orc):
     """128 substeps per step (physical-rate diffusion reading): 64 fused passes
-    per step equal the substep path bit for bit, and the oracle (cells
-    bit-exact, fields within 1e-4 of the medium value) after 30 steps."""
+    per step, and 32 passes of four substeps on the deep shapes, equal the
+    substep path bit for bit, and the oracle (cells bit-exact, fields within
+    1e-4 of the medium value) after 30 steps."""
     from paper_2303_08123_b300 import csr
     from synth.params import P_PHYS
     L, R, T = [16, 24], [3, 4], 30
     prot = [([2.0], [0.0]), ([1.0], [0.0])]
     out = []
-    for path in ("substep", "fused"):
-        sim = _sim(L, R, hours=1, t_end_steps=T, params=P_PHYS, path=path)
+    for kw in (dict(path="substep"), dict(path="fused"), dict(path="fused", tile_shape=8),
+               dict(path="fused", tile_shape=7)):
+        sim = _sim(L, R, hours=1, t_end_steps=T, params=P_PHYS, **kw)
         sim.load_protocols(*csr(prot))
         sim.run(0)
         out.append([sim.get_state(p) for p in range(2)])
         sim.close()
-    for a, b in zip(out[0], out[1]):
-        for x, y in zip(a, b):
-            assert np.array_equal(x, y)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
     for p in range(2):
         ref = orc.run(P_PHYS, L[p], R[p], SEED, p, prot[p][0], prot[p][1], t_end_steps=T)
         assert par.near_ratio(ref["stats"]) < par.NEAR_RATIO_MAX, ref["stats"]
