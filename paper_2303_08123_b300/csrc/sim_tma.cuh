@@ -52,7 +52,7 @@ template <int TX, int TY, int K, int HY>
 constexpr size_t tma_smem_bytes() {
     using S = TmaShape<TX, TY, K, HY>;
     return 128 + (size_t)kTmaStages * 4 * S::NB * sizeof(float) +
-           (size_t)((K > 1) ? K - 1 : 1) * 2 * S::NR * (sizeof(float2) + sizeof(float));
+           (size_t)((K > 1) ? K - 1 : 1) * 2 * S::THREADS * (sizeof(float2) + sizeof(float));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -66,23 +66,28 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-// true once the phase with the given parity has completed; false after the spin bound
+// true once the phase with the given parity has completed; false after the spin bound (2^22 tries).
+// The loop is written in PTX so that a wait that succeeds at once costs one try and one branch.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    for (int it = 0; it < (1 << 22); ++it) {
-        uint32_t done = 0;
-        asm volatile(
-            "{\n"
-            ".reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n"
-            "}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+    uint32_t done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        ".reg .u32 left;\n"
+        "mov.u32 left, %3;\n"
+        "TRY:\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "@p bra DONE;\n"
+        "sub.u32 left, left, 1;\n"
+        "setp.ne.u32 p, left, 0;\n"
+        "@p bra TRY;\n"
+        "DONE:\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1u << 22)
+        : "memory");
+    return done != 0;
 }
 
 // 3-D tiled bulk-tensor load of one box into shared memory, completing on `bar`
@@ -114,6 +119,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
           int pass, Params P) {
     using S = TmaShape<TX, TY, K, HY>;
     constexpr int BX = S::BX, NB = S::NB, RX = S::RX, RY = S::RY, NR = S::NR;
+    constexpr int NT = S::THREADS;  // stride of the level planes: one slot per thread, the idle tail included
     constexpr int kS = kTmaStages;
     constexpr uint32_t kStageBytes = 4u * NB * sizeof(float);
     extern __shared__ unsigned char smem_raw[];
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
     float* stage = reinterpret_cast<float*>(base);  // stage s: O2 [NB], glucose [NB], H+ [NB], cell words [NB]
     float2* lv_og = reinterpret_cast<float2*>(base + (size_t)kS * kStageBytes);
     float* lv_h = reinterpret_cast<float*>(base + (size_t)kS * kStageBytes +
-                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NR * sizeof(float2));
+                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NT * sizeof(float2));
     __shared__ __align__(8) uint64_t full[kS];
     __shared__ float s_dose, s_dq;
     __shared__ int s_tile;
@@ -135,9 +141,9 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
 #pragma unroll
     for (int l = 1; l <= K; ++l) inreg[l] = act && rx >= l - 1 && rx < RX - (l - 1) && ry >= l - 1 && ry < RY - (l - 1);
     const bool outtile = inreg[K];
-    // this thread's site in a staged plane
-    const int sb = (ry + HY - (K - 1)) * BX + (rx + kTmaHaloX - (K - 1));
-    float2* const my_lvog = lv_og + tid;  // + ((l - 1) * 2 + parity) * NR
+    // this thread's site in a staged plane (idle threads read thread 0's, so the loads need no guard)
+    const int sb = act ? (ry + HY - (K - 1)) * BX + (rx + kTmaHaloX - (K - 1)) : (HY - (K - 1)) * BX + kTmaHaloX - (K - 1);
+    float2* const my_lvog = lv_og + tid;  // + ((l - 1) * 2 + parity) * NT
     float* const my_lvh = lv_h + tid;
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
         float2 v0og = f2(0.f, 0.f);
         float v0h = 0.f;
         uint32_t w = 0;
-        if (loaded && act) {
+        if (loaded) {
             v0og = f2(st[sb], st[NB + sb]);
             v0h = st[2 * NB + sb];
             w = __float_as_uint(st[3 * NB + sb]);
@@ -272,63 +278,58 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
                 const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
                 reg = reg && q >= lo && q <= hi;
             }
-            float2 vog = f2(0.f, 0.f);
-            float vh = 0.f;
-            if (reg) {
-                const float2 cog = rog[l - 1][sq];
-                const float ch = rh[l - 1][sq];
-                if (fxy || (CHK && (q == 0 || q == L - 1))) {
+            // outside the level's region 0; on a face the value carried unchanged; else one substep
+            const float2 cog = rog[l - 1][sq];
+            const float ch = rh[l - 1][sq];
+            const bool face_q = fxy || (CHK && (q == 0 || q == L - 1));
+            float2 vog = reg ? cog : f2(0.f, 0.f);
+            float vh = reg ? ch : 0.f;
+            if (reg && !face_q) {
+                if (diffuse) {
+                    float2 xm, xp, ym, yp;
+                    float hxm, hxp, hym, hyp;
+                    if (l == 1) {  // level-0 neighbours from the staged plane q (planar arrays)
+                        const float* pq = stage + (size_t)((g0 + (uint32_t)(q - zl0)) & (kS - 1)) * 4 * NB + sb;
+                        xm = f2(pq[-1], pq[NB - 1]);
+                        xp = f2(pq[1], pq[NB + 1]);
+                        ym = f2(pq[-BX], pq[NB - BX]);
+                        yp = f2(pq[BX], pq[NB + BX]);
+                        hxm = pq[2 * NB - 1];
+                        hxp = pq[2 * NB + 1];
+                        hym = pq[2 * NB - BX];
+                        hyp = pq[2 * NB + BX];
+                    } else {  // level l-1 neighbours from its shared plane
+                        const int pj = (l >= 2 ? l - 2 : 0) * 2 + (q & 1);
+                        const float2* pog = my_lvog + pj * NT;
+                        const float* phh = my_lvh + pj * NT;
+                        xm = pog[-1];
+                        xp = pog[1];
+                        ym = pog[-RX];
+                        yp = pog[RX];
+                        hxm = phh[-1];
+                        hxp = phh[1];
+                        hym = phh[-RX];
+                        hyp = phh[RX];
+                    }
+                    vog = stencil_t2l(cog, xm, xp, ym, yp, rog[l - 1][sm], rog[l - 1][sp], lam_og);
+                    vh = stencil_t(ch, hxm, hxp, hym, hyp, rh[l - 1][sm], rh[l - 1][sp], P.lam[2]);
+                } else {
                     vog = cog;
                     vh = ch;
-                } else {
-                    if (diffuse) {
-                        float2 xm, xp, ym, yp;
-                        float hxm, hxp, hym, hyp;
-                        if (l == 1) {  // level-0 neighbours from the staged plane q (planar arrays)
-                            const float* pq = stage + (size_t)((g0 + (uint32_t)(q - zl0)) & (kS - 1)) * 4 * NB + sb;
-                            xm = f2(pq[-1], pq[NB - 1]);
-                            xp = f2(pq[1], pq[NB + 1]);
-                            ym = f2(pq[-BX], pq[NB - BX]);
-                            yp = f2(pq[BX], pq[NB + BX]);
-                            hxm = pq[2 * NB - 1];
-                            hxp = pq[2 * NB + 1];
-                            hym = pq[2 * NB - BX];
-                            hyp = pq[2 * NB + BX];
-                        } else {  // level l-1 neighbours from its shared plane
-                            const int pj = (l >= 2 ? l - 2 : 0) * 2 + (q & 1);
-                            const float2* pog = my_lvog + pj * NR;
-                            const float* phh = my_lvh + pj * NR;
-                            xm = pog[-1];
-                            xp = pog[1];
-                            ym = pog[-RX];
-                            yp = pog[RX];
-                            hxm = phh[-1];
-                            hxp = phh[1];
-                            hym = phh[-RX];
-                            hyp = phh[RX];
-                        }
-                        vog = stencil_t2l(cog, xm, xp, ym, yp, rog[l - 1][sm], rog[l - 1][sp], lam_og);
-                        vh = stencil_t(ch, hxm, hxp, hym, hyp, rh[l - 1][sm], rh[l - 1][sp], P.lam[2]);
-                    } else {
-                        vog = cog;
-                        vh = ch;
-                    }
-                    float uO = 0.f, uG = 0.f, pHv = 0.f;
-                    const uint32_t kq = wq & kKindMask;
-                    if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
-                    const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));  // v - u, lane by lane
-                    vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
-                    vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
                 }
+                float uO = 0.f, uG = 0.f, pHv = 0.f;
+                const uint32_t kq = wq & kKindMask;
+                if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
+                const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));  // v - u, lane by lane
+                vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
+                vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
             }
             if (l < K) {
                 const int pj = (l - 1) * 2 + (q & 1);
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
-                if (act) {
-                    my_lvog[pj * NR] = vog;
-                    my_lvh[pj * NR] = vh;
-                }
+                my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot
+                my_lvh[pj * NT] = vh;
             } else {
                 bool want = false;
                 const int o = q * LL;
