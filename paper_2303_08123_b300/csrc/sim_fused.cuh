@@ -426,11 +426,12 @@ struct FusedShape1 {
 
 constexpr int kStages1 = 8;  // stages of the one-column kernel (a power of two >= kDepth + 2)
 
-// stages: (O2, glucose) float2, H+ float, cell word per site; level planes: float2 + float per site
+// stages: (O2, glucose) float2, H+ float, cell word per site; level planes: float2 + float per thread
 template <int TX, int TY, int K>
 constexpr size_t fused1_smem_bytes() {
     using S = FusedShape1<TX, TY, K>;
-    return (size_t)kStages1 * S::NC * 4 * sizeof(float) + (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::NC * sizeof(float);
+    return (size_t)kStages1 * S::NC * 4 * sizeof(float) +
+           (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::THREADS * sizeof(float);
 }
 
 #ifndef SIM_FUSED1_MIN_BLOCKS_SMALL
@@ -453,6 +454,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
              uint32_t* __restrict__ tile_ctr, int n_tiles, int pass, Params P) {
     using S = FusedShape1<TX, TY, K>;
     constexpr int HX = S::HX, HY = S::HY, NC = S::NC;
+    constexpr int NT = S::THREADS;  // stride of the level planes: one slot per thread, the idle tail included
     constexpr int kS1 = kStages1;  // power of two: stage index = (plane - zl0) & (kS1 - 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stage_og = reinterpret_cast<float2*>(smem_raw);
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * NC * 3 * sizeof(float));
     float2* lv_og = reinterpret_cast<float2*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float));
     float* lv_h = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float) +
-                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NC * sizeof(float2));
+                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NT * sizeof(float2));
     __shared__ float s_dose, s_dq;  // the step's dose and its quadratic partner
     __shared__ int s_tile;
 
@@ -475,8 +477,9 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     float2* const my_og = stage_og + tid;      // + s * NC
     float* const my_h = stage_h + tid;         // + s * NC
     uint32_t* const my_cell = stage_c + tid;   // + s * NC
-    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NC
-    float* const my_lvh = lv_h + tid;          // + ((l - 1) * 2 + parity) * NC
+    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NT
+    float* const my_lvh = lv_h + tid;          // + ((l - 1) * 2 + parity) * NT
+    const int me = act ? tid : 0;              // idle threads read thread 0's staged site: no guard on the loads
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
     const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
@@ -563,10 +566,10 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
         float2 v0og = f2(0.f, 0.f);
         float v0h = 0.f;
         uint32_t w = 0;
-        if (loaded && act) {
-            v0og = my_og[st * NC];
-            v0h = my_h[st * NC];
-            w = my_cell[st * NC];
+        if (loaded) {
+            v0og = stage_og[me + st * NC];
+            v0h = stage_h[me + st * NC];
+            w = stage_c[me + st * NC];
         }
         if (dose > 0.f && loaded && !fxy && (!CHK || (i > 0 && i < L - 1)) && (w & kKindMask) != kEmpty) {
             const float Sv = lq_survival(w & kKindMask, v0og.x, dose, s_dq, P);
@@ -592,44 +595,39 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                 const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
                 reg = reg && q >= lo && q <= hi;
             }
-            float2 vog = f2(0.f, 0.f);
-            float vh = 0.f;
-            if (reg) {
-                const float2 cog = rog[l - 1][sq];
-                const float ch = rh[l - 1][sq];
-                if (fxy || (CHK && (q == 0 || q == L - 1))) {
+            // outside the level's region 0; on a face the value carried unchanged; else one substep
+            const float2 cog = rog[l - 1][sq];
+            const float ch = rh[l - 1][sq];
+            const bool face_q = fxy || (CHK && (q == 0 || q == L - 1));
+            float2 vog = reg ? cog : f2(0.f, 0.f);
+            float vh = reg ? ch : 0.f;
+            if (reg && !face_q) {
+                // level l-1 plane q: the stage of plane q (l = 1) or the shared plane of level l-1
+                const int pj = (l == 1) ? ((q - zl0) & (kS1 - 1)) : ((l >= 2 ? l - 2 : 0) * 2 + (q & 1));
+                const float2* pog = ((l == 1) ? my_og : my_lvog) + pj * ((l == 1) ? NC : NT);
+                const float* phh = ((l == 1) ? my_h : my_lvh) + pj * ((l == 1) ? NC : NT);
+                if (diffuse) {
+                    vog = stencil_t2l(cog, pog[-1], pog[1], pog[-HX], pog[HX], rog[l - 1][sm], rog[l - 1][sp],
+                                      lam_og);
+                    vh = stencil_t(ch, phh[-1], phh[1], phh[-HX], phh[HX], rh[l - 1][sm], rh[l - 1][sp],
+                                   P.lam[2]);
+                } else {
                     vog = cog;
                     vh = ch;
-                } else {
-                    // level l-1 plane q: the stage of plane q (l = 1) or the shared plane of level l-1
-                    const int pj = (l == 1) ? ((q - zl0) & (kS1 - 1)) : ((l >= 2 ? l - 2 : 0) * 2 + (q & 1));
-                    const float2* pog = ((l == 1) ? my_og : my_lvog) + pj * NC;
-                    const float* phh = ((l == 1) ? my_h : my_lvh) + pj * NC;
-                    if (diffuse) {
-                        vog = stencil_t2l(cog, pog[-1], pog[1], pog[-HX], pog[HX], rog[l - 1][sm], rog[l - 1][sp],
-                                          lam_og);
-                        vh = stencil_t(ch, phh[-1], phh[1], phh[-HX], phh[HX], rh[l - 1][sm], rh[l - 1][sp],
-                                       P.lam[2]);
-                    } else {
-                        vog = cog;
-                        vh = ch;
-                    }
-                    float uO = 0.f, uG = 0.f, pHv = 0.f;
-                    const uint32_t kq = wr[sq] & kKindMask;
-                    if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
-                    const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));  // v - u, lane by lane
-                    vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
-                    vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
                 }
+                float uO = 0.f, uG = 0.f, pHv = 0.f;
+                const uint32_t kq = wr[sq] & kKindMask;
+                if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
+                const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));  // v - u, lane by lane
+                vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
+                vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
             }
             if (l < K) {
                 const int pj = (l - 1) * 2 + (q & 1);
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
-                if (act) {
-                    my_lvog[pj * NC] = vog;
-                    my_lvh[pj * NC] = vh;
-                }
+                my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot
+                my_lvh[pj * NT] = vh;
             } else {
                 bool want = false;
                 const int o = q * LL;

@@ -96,7 +96,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 }
 
 #ifndef SIM_TMA_MIN_BLOCKS_SMALL
-#define SIM_TMA_MIN_BLOCKS_SMALL 2  // CTAs per SM the 16 x 16 TMA kernel is register-budgeted for
+#define SIM_TMA_MIN_BLOCKS_SMALL 3  // CTAs per SM the 16 x 16 TMA kernel is register-budgeted for
 #endif
 #ifndef SIM_TMA_MIN_BLOCKS_DEEP
 #define SIM_TMA_MIN_BLOCKS_DEEP 1  // the same for its passes of four substeps
