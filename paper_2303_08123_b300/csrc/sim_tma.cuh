@@ -15,7 +15,17 @@
 //     and field halo of a lattice edge needs (such sites are faces and never
 //     feed an interior site);
 //   * the thread grid covers only the level-1 region (the tile plus K - 1
-//     columns), not the outer halo the copies used to need a thread for.
+//     columns), not the outer halo the copies used to need a thread for;
+//   * on the 32 x 16 tiles, whose CTA has an SM to itself, no CTA-wide
+//     barrier per plane: the level planes the threads exchange live in a ring
+//     of three slots per level, every thread arrives on one mbarrier after its
+//     level-plane stores of a plane iteration and, in the next iteration,
+//     waits for that phase only before its own first store (and before the
+//     stage refill), so warps may drift apart by most of an iteration instead
+//     of meeting at the top of each one (9-10 % faster); the 16 x 16 tiles run
+//     three CTAs per SM, which hide each other's barrier waits, and keep one
+//     __syncthreads per plane with two slots (the mbarrier measured 11-13 %
+//     slower there).
 // One tensor map per (lattice side, array, tile shape) addresses each array as
 // an L x L x Z volume; every protocol's first site is a multiple of L^2, so the
 // protocol's planes are whole z-slices of that volume.
@@ -36,6 +46,8 @@ constexpr uint32_t kStatusTmaTimeout = 8u;  // a stage's copies did not land wit
 // HY: rows of halo the staged box carries above and below the tile (the deepest pass it serves)
 template <int TX, int TY, int K, int HY>
 struct TmaShape {
+    static constexpr bool PLANE_BAR = TX * TY > 256;  // mbarrier-paced planes (see above), else a CTA barrier
+    static constexpr int SLOTS = PLANE_BAR ? 3 : 2;     // level-plane slots per level
     static constexpr int BX = TX + 2 * kTmaHaloX;  // staged box (x extent)
     static constexpr int BY = TY + 2 * HY;         // staged box (y extent)
     static constexpr int NB = BX * BY;             // sites of one staged plane
@@ -52,13 +64,17 @@ template <int TX, int TY, int K, int HY>
 constexpr size_t tma_smem_bytes() {
     using S = TmaShape<TX, TY, K, HY>;
     return 128 + (size_t)kTmaStages * 4 * S::NB * sizeof(float) +
-           (size_t)((K > 1) ? K - 1 : 1) * 2 * S::THREADS * (sizeof(float2) + sizeof(float));
+           (size_t)((K > 1) ? K - 1 : 1) * S::SLOTS * S::THREADS * (sizeof(float2) + sizeof(float));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -124,8 +140,9 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
     float* stage = reinterpret_cast<float*>(base);  // stage s: O2 [NB], glucose [NB], H+ [NB], cell words [NB]
     float2* lv_og = reinterpret_cast<float2*>(base + (size_t)kS * kStageBytes);
     float* lv_h = reinterpret_cast<float*>(base + (size_t)kS * kStageBytes +
-                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NT * sizeof(float2));
+                                           (size_t)((K > 1) ? K - 1 : 1) * S::SLOTS * NT * sizeof(float2));
     __shared__ __align__(8) uint64_t full[kS];
+    __shared__ __align__(8) uint64_t plane_bar;  // every thread arrives once per plane iteration
     __shared__ float s_dose, s_dq;
     __shared__ int s_tile;
 
@@ -146,8 +163,11 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
     const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
     bool timed_out = false;
 
-    if (tid == 0)
+    if (tid == 0) {
         for (int s = 0; s < kS; ++s) mbar_init(&full[s], 1);
+        mbar_init(&plane_bar, NT);
+    }
+    uint32_t n_sync = 0;  // plane iterations this thread has arrived for (plane_bar phases)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     __syncthreads();
 
@@ -229,8 +249,10 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
     auto iteration = [&](auto phc, auto chkc, const int i) {
         constexpr int ph = decltype(phc)::value;
         constexpr bool CHK = decltype(chkc)::value;
-        __syncthreads();  // iteration i - 1 is done everywhere: its stage reads and level-plane writes
-        issue(i + kDepth);
+        if constexpr (!S::PLANE_BAR) {
+            __syncthreads();  // iteration i - 1 is done everywhere: its stage reads and level-plane writes
+            issue(i + kDepth);
+        }
         const bool loaded = !CHK || i <= zl1;
         const uint32_t n = g0 + (uint32_t)(i - zl0);
         const float* st = stage + (size_t)(n & (kS - 1)) * 4 * NB;
@@ -295,7 +317,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
                         hym = pq[2 * NB - BX];
                         hyp = pq[2 * NB + BX];
                     } else {  // level l-1 neighbours from its shared plane
-                        const int pj = (l >= 2 ? l - 2 : 0) * 2 + (q & 1);
+                        const int pj = (l >= 2 ? l - 2 : 0) * S::SLOTS + (S::PLANE_BAR ? sq : (q & 1));
                         const float2* pog = my_lvog + pj * NT;
                         const float* phh = my_lvh + pj * NT;
                         xm = pog[-1];
@@ -320,8 +342,18 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
                 vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
                 vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
             }
+            if (S::PLANE_BAR && l == 1) {
+                // every thread has finished the previous iteration (its stage reads, level-plane stores and
+                // reads): the level-plane slots of plane q - 3 and the stage of plane i - 4 are free again
+                if (n_sync > 0 && !timed_out && !mbar_wait(&plane_bar, (n_sync - 1) & 1u)) {
+                    timed_out = true;
+                    if (P.status) atomicOr(P.status, kStatusTmaTimeout);
+                }
+                issue(i + kDepth);
+            }
             if (l < K) {
-                const int pj = (l - 1) * 2 + (q & 1);
+                // level l, plane q: slot (q - zl0) mod 3 (mbarrier-paced) or q mod 2
+                const int pj = (l - 1) * S::SLOTS + (S::PLANE_BAR ? sq : (q & 1));
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
                 my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot
@@ -353,6 +385,10 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
                         if (want && site_ok(P, at)) intents[at] = (uint32_t)(pr.site0 + col + o);
                     }
                 }
+            }
+            if (S::PLANE_BAR && l == (K > 1 ? K - 1 : 1)) {  // this thread's level-plane stores and stage reads
+                mbar_arrive(&plane_bar);
+                ++n_sync;
             }
         }
     };
