@@ -27,18 +27,22 @@ __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) { return 
 template <>
 __device__ __forceinline__ float widen<__half>(__half v) { return __half2float(v); }
 
-// stages: 3 fields of T and a cell word per site; level planes: float2 + float per site
+// stages: 3 fields of T and a cell word per site; level planes: float2 + float per thread
 template <typename T, int TX, int TY, int K>
 constexpr size_t fused1h_smem_bytes() {
     using S = FusedShape1<TX, TY, K>;
     return (size_t)kStages1 * S::NC * (3 * sizeof(T) + sizeof(uint32_t)) +
-           (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::NC * sizeof(float);
+           (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::THREADS * sizeof(float);
 }
+
+#ifndef SIM_FUSED1H_MIN_BLOCKS_SMALL
+#define SIM_FUSED1H_MIN_BLOCKS_SMALL 2  // CTAs per SM the 16 x 16 two-byte kernel is register-budgeted for
+#endif
 
 // FULL as in k_fused1: diffusion and reaction switches fixed on at compile time.
 template <typename T, int TX, int TY, int K, bool EPI, bool FULL>
 __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
-                                  (TX * TY <= 256) ? SIM_FUSED1_MIN_BLOCKS_SMALL : SIM_FUSED1_MIN_BLOCKS_LARGE)
+                                  (TX * TY <= 256) ? SIM_FUSED1H_MIN_BLOCKS_SMALL : SIM_FUSED1_MIN_BLOCKS_LARGE)
     k_fused1h(const Tile* __restrict__ tiles, const Proto* __restrict__ protos, const int64_t* __restrict__ clock,
               int k_off, int first, const T* __restrict__ iO, const T* __restrict__ iG, const T* __restrict__ iH,
               T* __restrict__ oO, T* __restrict__ oG, T* __restrict__ oH, const uint32_t* cin, uint32_t* cout,
@@ -47,6 +51,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
               int n_tiles, int pass, Params P) {
     using S = FusedShape1<TX, TY, K>;
     constexpr int HX = S::HX, HY = S::HY, NC = S::NC;
+    constexpr int NT = S::THREADS;  // stride of the level planes: one slot per thread, the idle tail included
     static_assert(HX % 2 == 0 && NC % 2 == 0, "element pairs must not straddle rows or planes");
     constexpr int kS1 = kStages1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -54,7 +59,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * 3 * NC * sizeof(T));
     unsigned char* lv_raw = smem_raw + (size_t)kS1 * NC * (3 * sizeof(T) + sizeof(uint32_t));
     float2* lv_og = reinterpret_cast<float2*>(lv_raw);
-    float* lv_h = reinterpret_cast<float*>(lv_raw + (size_t)((K > 1) ? K - 1 : 1) * 2 * NC * sizeof(float2));
+    float* lv_h = reinterpret_cast<float*>(lv_raw + (size_t)((K > 1) ? K - 1 : 1) * 2 * NT * sizeof(float2));
     __shared__ float s_dose, s_dq;
     __shared__ int s_tile;
 
@@ -68,8 +73,9 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     const bool outtile = act && cx >= K && cx < K + TX && cy >= K && cy < K + TY;
     T* const my_t = stage_t + tid;             // + (s * 3 + f) * NC
     uint32_t* const my_cell = stage_c + tid;   // + s * NC
-    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NC
+    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NT
     float* const my_lvh = lv_h + tid;
+    const int me = act ? tid : 0;              // idle threads read thread 0's staged site: no guard on the loads
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
     const bool diffuse = FULL || (P.flags & kFDiffusion) != 0, react = FULL || (P.flags & kFReaction) != 0;
@@ -152,11 +158,11 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
         float2 v0og = f2(0.f, 0.f);
         float v0h = 0.f;
         uint32_t w = 0;
-        if (loaded && act) {
-            const T* sf = my_t + st * 3 * NC;
+        if (loaded) {
+            const T* sf = stage_t + me + st * 3 * NC;
             v0og = f2(widen<T>(sf[0]), widen<T>(sf[NC]));
             v0h = widen<T>(sf[2 * NC]);
-            w = my_cell[st * NC];
+            w = stage_c[me + st * NC];
         }
         if (dose > 0.f && loaded && !fxy && (!CHK || (i > 0 && i < L - 1)) && (w & kKindMask) != kEmpty) {
             const float Sv = lq_survival(w & kKindMask, v0og.x, dose, s_dq, P);
@@ -182,56 +188,51 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                 const int hi = (zl1 == L - 1) ? L - 1 : zl1 - l;
                 reg = reg && q >= lo && q <= hi;
             }
-            float2 vog = f2(0.f, 0.f);
-            float vh = 0.f;
-            if (reg) {
-                const float2 cog = rog[l - 1][sq];
-                const float ch = rh[l - 1][sq];
-                if (fxy || (CHK && (q == 0 || q == L - 1))) {
+            // outside the level's region 0; on a face the value carried unchanged; else one substep
+            const float2 cog = rog[l - 1][sq];
+            const float ch = rh[l - 1][sq];
+            const bool face_q = fxy || (CHK && (q == 0 || q == L - 1));
+            float2 vog = reg ? cog : f2(0.f, 0.f);
+            float vh = reg ? ch : 0.f;
+            if (reg && !face_q) {
+                if (diffuse) {
+                    if (l == 1) {  // neighbours from the stage of plane q, widened to FP32
+                        const T* so = my_t + ((q - zl0) & (kS1 - 1)) * 3 * NC;
+                        const T* sg = so + NC;
+                        const T* sh = so + 2 * NC;
+                        vog = stencil_t2l(cog, f2(widen<T>(so[-1]), widen<T>(sg[-1])),
+                                          f2(widen<T>(so[1]), widen<T>(sg[1])),
+                                          f2(widen<T>(so[-HX]), widen<T>(sg[-HX])),
+                                          f2(widen<T>(so[HX]), widen<T>(sg[HX])), rog[l - 1][sm],
+                                          rog[l - 1][sp], lam_og);
+                        vh = stencil_t(ch, widen<T>(sh[-1]), widen<T>(sh[1]), widen<T>(sh[-HX]),
+                                       widen<T>(sh[HX]), rh[l - 1][sm], rh[l - 1][sp], P.lam[2]);
+                    } else {  // neighbours from the shared plane of level l-1 (FP32)
+                        const int pj = (l >= 2 ? l - 2 : 0) * 2 + (q & 1);
+                        const float2* pog = my_lvog + pj * NT;
+                        const float* phh = my_lvh + pj * NT;
+                        vog = stencil_t2l(cog, pog[-1], pog[1], pog[-HX], pog[HX], rog[l - 1][sm],
+                                          rog[l - 1][sp], lam_og);
+                        vh = stencil_t(ch, phh[-1], phh[1], phh[-HX], phh[HX], rh[l - 1][sm], rh[l - 1][sp],
+                                       P.lam[2]);
+                    }
+                } else {
                     vog = cog;
                     vh = ch;
-                } else {
-                    if (diffuse) {
-                        if (l == 1) {  // neighbours from the stage of plane q, widened to FP32
-                            const T* so = my_t + ((q - zl0) & (kS1 - 1)) * 3 * NC;
-                            const T* sg = so + NC;
-                            const T* sh = so + 2 * NC;
-                            vog = stencil_t2l(cog, f2(widen<T>(so[-1]), widen<T>(sg[-1])),
-                                              f2(widen<T>(so[1]), widen<T>(sg[1])),
-                                              f2(widen<T>(so[-HX]), widen<T>(sg[-HX])),
-                                              f2(widen<T>(so[HX]), widen<T>(sg[HX])), rog[l - 1][sm],
-                                              rog[l - 1][sp], lam_og);
-                            vh = stencil_t(ch, widen<T>(sh[-1]), widen<T>(sh[1]), widen<T>(sh[-HX]),
-                                           widen<T>(sh[HX]), rh[l - 1][sm], rh[l - 1][sp], P.lam[2]);
-                        } else {  // neighbours from the shared plane of level l-1 (FP32)
-                            const int pj = (l >= 2 ? l - 2 : 0) * 2 + (q & 1);
-                            const float2* pog = my_lvog + pj * NC;
-                            const float* phh = my_lvh + pj * NC;
-                            vog = stencil_t2l(cog, pog[-1], pog[1], pog[-HX], pog[HX], rog[l - 1][sm],
-                                              rog[l - 1][sp], lam_og);
-                            vh = stencil_t(ch, phh[-1], phh[1], phh[-HX], phh[HX], rh[l - 1][sm], rh[l - 1][sp],
-                                           P.lam[2]);
-                        }
-                    } else {
-                        vog = cog;
-                        vh = ch;
-                    }
-                    float uO = 0.f, uG = 0.f, pHv = 0.f;
-                    const uint32_t kq = wr[sq] & kKindMask;
-                    if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
-                    const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));
-                    vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
-                    vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
                 }
+                float uO = 0.f, uG = 0.f, pHv = 0.f;
+                const uint32_t kq = wr[sq] & kKindMask;
+                if (react && kq != kEmpty) uptake(kq, cog.x, cog.y, P, uO, uG, pHv);
+                const float2 o2 = __fadd2_rn(vog, f2(-uO, -uG));
+                vog = f2(fmaxf(o2.x, 0.f), fmaxf(o2.y, 0.f));
+                vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
             }
             if (l < K) {
                 const int pj = (l - 1) * 2 + (q & 1);
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
-                if (act) {
-                    my_lvog[pj * NC] = vog;
-                    my_lvh[pj * NC] = vh;
-                }
+                my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot
+                my_lvh[pj * NT] = vh;
             } else {
                 bool want = false;
                 const int o = q * LL;
