@@ -24,8 +24,9 @@
 //     stage refill), so warps may drift apart by most of an iteration instead
 //     of meeting at the top of each one (9-10 % faster); the 16 x 16 tiles run
 //     three CTAs per SM, which hide each other's barrier waits, and keep one
-//     __syncthreads per plane with two slots (the mbarrier measured 11-13 %
-//     slower there).
+//     __syncthreads per plane (the mbarrier measured 11-13 % slower there);
+//     both use the three-slot ring, whose slot offsets the x3 unrolled z loop
+//     fixes at compile time (2 % faster than two slots indexed by plane parity).
 // One tensor map per (lattice side, array, tile shape) addresses each array as
 // an L x L x Z volume; every protocol's first site is a multiple of L^2, so the
 // protocol's planes are whole z-slices of that volume.
@@ -47,7 +48,7 @@ constexpr uint32_t kStatusTmaTimeout = 8u;  // a stage's copies did not land wit
 template <int TX, int TY, int K, int HY>
 struct TmaShape {
     static constexpr bool PLANE_BAR = TX * TY > 256;  // mbarrier-paced planes (see above), else a CTA barrier
-    static constexpr int SLOTS = PLANE_BAR ? 3 : 2;     // level-plane slots per level
+    static constexpr int SLOTS = 3;                    // level-plane slots per level: plane (q - zl0) mod 3
     static constexpr int BX = TX + 2 * kTmaHaloX;  // staged box (x extent)
     static constexpr int BY = TY + 2 * HY;         // staged box (y extent)
     static constexpr int NB = BX * BY;             // sites of one staged plane
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
                         hym = pq[2 * NB - BX];
                         hyp = pq[2 * NB + BX];
                     } else {  // level l-1 neighbours from its shared plane
-                        const int pj = (l >= 2 ? l - 2 : 0) * S::SLOTS + (S::PLANE_BAR ? sq : (q & 1));
+                        const int pj = (l >= 2 ? l - 2 : 0) * S::SLOTS + sq;
                         const float2* pog = my_lvog + pj * NT;
                         const float* phh = my_lvh + pj * NT;
                         xm = pog[-1];
@@ -352,8 +353,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
                 issue(i + kDepth);
             }
             if (l < K) {
-                // level l, plane q: slot (q - zl0) mod 3 (mbarrier-paced) or q mod 2
-                const int pj = (l - 1) * S::SLOTS + (S::PLANE_BAR ? sq : (q & 1));
+                const int pj = (l - 1) * S::SLOTS + sq;  // level l, plane q: slot (q - zl0) mod 3
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
                 my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot
