@@ -426,12 +426,13 @@ struct FusedShape1 {
 
 constexpr int kStages1 = 8;  // stages of the one-column kernel (a power of two >= kDepth + 2)
 
-// stages: (O2, glucose) float2, H+ float, cell word per site; level planes: float2 + float per thread
+// stages: (O2, glucose) float2, H+ float, cell word per site; level planes: float2 + float per thread, three
+// slots per level (plane (q - zl0) mod 3)
 template <int TX, int TY, int K>
 constexpr size_t fused1_smem_bytes() {
     using S = FusedShape1<TX, TY, K>;
     return (size_t)kStages1 * S::NC * 4 * sizeof(float) +
-           (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::THREADS * sizeof(float);
+           (size_t)((K > 1) ? K - 1 : 1) * 3 * 3 * S::THREADS * sizeof(float);
 }
 
 #ifndef SIM_FUSED1_MIN_BLOCKS_SMALL
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * NC * 3 * sizeof(float));
     float2* lv_og = reinterpret_cast<float2*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float));
     float* lv_h = reinterpret_cast<float*>(smem_raw + (size_t)kS1 * NC * 4 * sizeof(float) +
-                                           (size_t)((K > 1) ? K - 1 : 1) * 2 * NT * sizeof(float2));
+                                           (size_t)((K > 1) ? K - 1 : 1) * 3 * NT * sizeof(float2));
     __shared__ float s_dose, s_dq;  // the step's dose and its quadratic partner
     __shared__ int s_tile;
 
@@ -477,8 +478,8 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     float2* const my_og = stage_og + tid;      // + s * NC
     float* const my_h = stage_h + tid;         // + s * NC
     uint32_t* const my_cell = stage_c + tid;   // + s * NC
-    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NT
-    float* const my_lvh = lv_h + tid;          // + ((l - 1) * 2 + parity) * NT
+    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 3 + slot) * NT
+    float* const my_lvh = lv_h + tid;          // + ((l - 1) * 3 + slot) * NT
     const int me = act ? tid : 0;              // idle threads read thread 0's staged site: no guard on the loads
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
             float vh = reg ? ch : 0.f;
             if (reg && !face_q) {
                 // level l-1 plane q: the stage of plane q (l = 1) or the shared plane of level l-1
-                const int pj = (l == 1) ? ((q - zl0) & (kS1 - 1)) : ((l >= 2 ? l - 2 : 0) * 2 + (q & 1));
+                const int pj = (l == 1) ? ((q - zl0) & (kS1 - 1)) : ((l >= 2 ? l - 2 : 0) * 3 + sq);
                 const float2* pog = ((l == 1) ? my_og : my_lvog) + pj * ((l == 1) ? NC : NT);
                 const float* phh = ((l == 1) ? my_h : my_lvh) + pj * ((l == 1) ? NC : NT);
                 if (diffuse) {
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                 vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
             }
             if (l < K) {
-                const int pj = (l - 1) * 2 + (q & 1);
+                const int pj = (l - 1) * 3 + sq;  // level l, plane q: slot (q - zl0) mod 3, fixed by the unroll
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
                 my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot

@@ -27,12 +27,12 @@ __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) { return 
 template <>
 __device__ __forceinline__ float widen<__half>(__half v) { return __half2float(v); }
 
-// stages: 3 fields of T and a cell word per site; level planes: float2 + float per thread
+// stages: 3 fields of T and a cell word per site; level planes: float2 + float per thread, three slots per level
 template <typename T, int TX, int TY, int K>
 constexpr size_t fused1h_smem_bytes() {
     using S = FusedShape1<TX, TY, K>;
     return (size_t)kStages1 * S::NC * (3 * sizeof(T) + sizeof(uint32_t)) +
-           (size_t)((K > 1) ? K - 1 : 1) * 2 * 3 * S::THREADS * sizeof(float);
+           (size_t)((K > 1) ? K - 1 : 1) * 3 * 3 * S::THREADS * sizeof(float);
 }
 
 #ifndef SIM_FUSED1H_MIN_BLOCKS_SMALL
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     uint32_t* stage_c = reinterpret_cast<uint32_t*>(smem_raw + (size_t)kS1 * 3 * NC * sizeof(T));
     unsigned char* lv_raw = smem_raw + (size_t)kS1 * NC * (3 * sizeof(T) + sizeof(uint32_t));
     float2* lv_og = reinterpret_cast<float2*>(lv_raw);
-    float* lv_h = reinterpret_cast<float*>(lv_raw + (size_t)((K > 1) ? K - 1 : 1) * 2 * NT * sizeof(float2));
+    float* lv_h = reinterpret_cast<float*>(lv_raw + (size_t)((K > 1) ? K - 1 : 1) * 3 * NT * sizeof(float2));
     __shared__ float s_dose, s_dq;
     __shared__ int s_tile;
 
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
     const bool outtile = act && cx >= K && cx < K + TX && cy >= K && cy < K + TY;
     T* const my_t = stage_t + tid;             // + (s * 3 + f) * NC
     uint32_t* const my_cell = stage_c + tid;   // + s * NC
-    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 2 + parity) * NT
+    float2* const my_lvog = lv_og + tid;       // + ((l - 1) * 3 + slot) * NT
     float* const my_lvh = lv_h + tid;
     const int me = act ? tid : 0;              // idle threads read thread 0's staged site: no guard on the loads
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                         vh = stencil_t(ch, widen<T>(sh[-1]), widen<T>(sh[1]), widen<T>(sh[-HX]),
                                        widen<T>(sh[HX]), rh[l - 1][sm], rh[l - 1][sp], P.lam[2]);
                     } else {  // neighbours from the shared plane of level l-1 (FP32)
-                        const int pj = (l >= 2 ? l - 2 : 0) * 2 + (q & 1);
+                        const int pj = (l >= 2 ? l - 2 : 0) * 3 + sq;
                         const float2* pog = my_lvog + pj * NT;
                         const float* phh = my_lvh + pj * NT;
                         vog = stencil_t2l(cog, pog[-1], pog[1], pog[-HX], pog[HX], rog[l - 1][sm],
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(FusedShape1<TX, TY, K>::THREADS,
                 vh = fmaxf(__fadd_rn(vh, pHv), 0.f);
             }
             if (l < K) {
-                const int pj = (l - 1) * 2 + (q & 1);
+                const int pj = (l - 1) * 3 + sq;  // level l, plane q: slot (q - zl0) mod 3, fixed by the unroll
                 rog[l][sq] = vog;
                 rh[l][sq] = vh;
                 my_lvog[pj * NT] = vog;  // idle threads write their own (never read) slot
