@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
     for (int l = 1; l <= K; ++l) inreg[l] = act && rx >= l - 1 && rx < RX - (l - 1) && ry >= l - 1 && ry < RY - (l - 1);
     const bool outtile = inreg[K];
     // this thread's site in a staged plane (idle threads read thread 0's, so the loads need no guard)
-    const int sb = act ? (ry + HY - (K - 1)) * BX + (rx + kTmaHaloX - (K - 1)) : (HY - (K - 1)) * BX + kTmaHaloX - (K - 1);
-    float2* const my_lvog = lv_og + tid;  // + ((l - 1) * 2 + parity) * NT
+    const int sb0 = (HY - (K - 1)) * BX + kTmaHaloX - (K - 1);  // the level-1 region's first site
+    const int sb = act ? sb0 + ry * BX + rx : sb0;
+    float2* const my_lvog = lv_og + tid;  // + ((l - 1) * 3 + slot) * NT
     float* const my_lvh = lv_h + tid;
     const float2 lam_og = f2(P.lam[0], P.lam[1]);
     const uint32_t lane = threadIdx.x & 31u;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(TmaShape<TX, TY, K, HY>::THREADS,
 
     if (tid == 0) {
         for (int s = 0; s < kS; ++s) mbar_init(&full[s], 1);
-        mbar_init(&plane_bar, NT);
+        if (S::PLANE_BAR) mbar_init(&plane_bar, NT);
     }
     uint32_t n_sync = 0;  // plane iterations this thread has arrived for (plane_bar phases)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
